@@ -1,0 +1,455 @@
+#!/usr/bin/env python
+"""Benchmark of the 3D Fourier insertion hot path on GB300.
+
+Workload (stand-in for the large reconstruction of Sec. 5.3.2): S = 256
+images (129 x 256 complex half planes), batches of 5000 images, a 257^3
+volume, Kaiser-Bessel blob a = 1.9, alpha = 15, 10000-entry table.  A step is
+one fr_insert of one resident batch (every step of the path runs in the
+library's CUDA kernels).  The metric is voxel-updates/s: one update is one
+(pixel, voxel) pair with |v - q| <= a inside the volume, counted exactly by
+fr_count_updates.
+
+Phases (one JSON line at the end):
+  untuned  the library's default configuration, no tuning;
+  tuning   cold-start non-blocking dynamic tuning (exhaustive search, four
+           configurations per insert) until the space is exhausted; reports
+           the tuning overhead of Eq. (performance) (Sec. 5.4);
+  tuned    the configuration the tuner chose -- the headline `value`;
+  e2e      the tuned path with host-resident (pinned) inputs copied in every
+           step, the device status word read back every step, and the final
+           volume downloaded once at the end of the timed region.
+
+--impl reference times the FP64 CPU oracle (the definition, written as a
+plain scatter) on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Fourier-insertion voxel-updates/s at S=256 (tuned vs untuned); tuning overhead %"
+UNIT = "voxel-updates/s"
+FLOPS_PER_UPDATE = 16  # algorithmic FP32 flops per update (3 sub, 5 for r^2, 3 table lerp, 5 accumulate)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--dtype", default="f32", choices=["f32", "f16"])
+    p.add_argument("--S", type=int, default=256)
+    p.add_argument("--n", type=int, default=5000)
+    p.add_argument("--batches", type=int, default=4, help="distinct resident batches, cycled")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="target oracle work for cpu_baseline")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--seed", type=int, default=5)
+    return p.parse_args()
+
+
+def workload_name(S, n, dtype):
+    return f"3D Fourier insertion, S={S} ({S // 2 + 1}x{S} complex {dtype.upper()} half planes), " \
+           f"batches of {n} images, {S + 1}^3 volume, blob a=1.9 alpha=15 table 10000"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        res = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return res
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]) if parts[3] not in ("[N/A]", "N/A") else 0.0,
+                             parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return res
+        mx = max(r[1] for r in rows)
+        loaded = [r for r in rows if r[2] > 0.25 * max(x[2] for x in rows)] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in loaded for i, v in enumerate(r[3]) if v.lower() == "active"})
+        res.update(sm_mhz=statistics.median(r[0] for r in loaded), sm_max_mhz=mx, reasons=reasons,
+                   samples=len(rows))
+        return res
+
+
+# ------------------------------------------------------------------ distributed helpers
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int, device) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+
+def oracle_sample(S, img_cpu, rot_cpu, target_s, a):
+    """Time the FP64 oracle on the first m images, m sized for ~target_s of work."""
+    import oracle
+    oracle.build()
+    nt = oracle.max_threads()
+    m0 = 4
+    t0 = time.perf_counter()
+    _, _, c0 = oracle.insert(S, img_cpu[:m0], rot_cpu[:m0], a=a, alpha=15.0, nthreads=nt)
+    dt0 = time.perf_counter() - t0
+    m = int(max(m0, min(img_cpu.shape[0], m0 * target_s / max(dt0, 1e-3))))
+    t1 = time.perf_counter()
+    _, _, c = oracle.insert(S, img_cpu[:m], rot_cpu[:m], a=a, alpha=15.0, nthreads=nt)
+    dt = time.perf_counter() - t1
+    return {"value": c / dt, "unit": UNIT, "cores": nt, "kind": "oracle",
+            "sample": f"first {m} images of batch 0 ({c} updates, {dt:.1f} s, FP64 scatter, OpenMP z-slab "
+                      f"ownership, {nt} threads)"}
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    from paper_1910_08498_gb300 import inputs
+    oracle.build()
+    S, n = args.S, args.n
+    a = float(np.float32(1.9))
+    img, rot = inputs.make_batch(S, n, args.seed)
+    img, rot = img.numpy(), rot.numpy()
+    nt = oracle.max_threads()
+    # size one step for ~8 s of oracle work
+    t0 = time.perf_counter()
+    _, _, c0 = oracle.insert(S, img[:2], rot[:2], a=a, nthreads=nt)
+    per_img = (time.perf_counter() - t0) / 2
+    m = int(max(1, min(n, 8.0 / max(per_img, 1e-4))))
+    times, ups = [], []
+    for step in range(args.warmup + args.steps):
+        lo = (step * m) % max(1, n - m + 1)
+        t = time.perf_counter()
+        _, _, c = oracle.insert(S, img[lo:lo + m], rot[lo:lo + m], a=a, nthreads=nt)
+        dt = time.perf_counter() - t
+        if step >= args.warmup:
+            times.append(dt)
+            ups.append(c)
+    total_t = sum(times)
+    value = sum(ups) / total_t
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_t / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": workload_name(S, n, args.dtype), "S": S, "n_per_step": m,
+                       "parallelism": "host threads"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
+                             "sample": f"{m} images per step (of a {n}-image batch), FP64 scatter"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1910_08498_gb300 import _lib as L
+    from paper_1910_08498_gb300 import inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    L.lib()
+    S, n, NB = args.S, args.n, args.batches
+    a = float(np.float32(1.9))
+    f16 = args.dtype == "f16"
+    stream = torch.cuda.current_stream()
+
+    # resident inputs (each batch 1.32 GB in FP32: larger than L2, cycled)
+    batches = []
+    for b in range(NB):
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(args.seed * 1000 + 97 * rank + b)
+        rot = inputs.random_rotations(n, gen, dev).contiguous()
+        img = inputs.random_images(S, n, gen, dev)
+        img = inputs.to_half(img) if f16 else img.contiguous()
+        batches.append((img, rot))
+    ctx = L.fr_create(S, a, 15.0, 0, 10000)
+    updates = [L.fr_count_updates(ctx, rot) for _, rot in batches]
+    img_bytes = batches[0][0].numel() * batches[0][0].element_size()
+    rot_bytes = batches[0][1].numel() * 4
+
+    def timed_steps(k, first=0):
+        """k inserts, batches cycled; returns (seconds, updates, per-launch ms list)."""
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        ups = 0
+        for i in range(k):
+            img, rot = batches[(first + i) % NB]
+            evs[i][0].record(stream)
+            L.fr_insert(ctx, img, rot)
+            evs[i][1].record(stream)
+            ups += updates[(first + i) % NB]
+        torch.cuda.synchronize()
+        ms = [s.elapsed_time(e) for s, e in evs]
+        return sum(ms) / 1e3, ups, ms
+
+    # ---- untuned: default configuration
+    L.fr_set_options(ctx, tuning=0, forced_config=-1)
+    timed_steps(args.warmup)
+    barrier(world)
+    torch.cuda.synchronize()
+    t_un, u_un, _ = timed_steps(args.steps)
+    t_un = max_over_ranks(t_un, world, dev)
+    untuned_cfg = L.fr_tuning_report(ctx)["last_config"]
+
+    # ---- tuning: cold start, exhaustive, non-blocking
+    L.fr_reset(ctx)
+    L.fr_retune(ctx, True)
+    L.fr_set_options(ctx, tuning=1, search=L.FR_SEARCH_EXHAUSTIVE, steps_per_insert=4, forced_config=-1)
+    tune_inserts = 0
+    t_tune = 0.0
+    u_tune = 0
+    while True:
+        dt, u, _ = timed_steps(1, tune_inserts)
+        t_tune += dt
+        u_tune += u
+        tune_inserts += 1
+        rep = L.fr_tuning_report(ctx)
+        if rep["tuned"] or tune_inserts >= 200:
+            break
+    rep_tune = L.fr_tuning_report(ctx)
+    best = rep_tune["best_config"]
+    space_avg_ns = rep_tune["mean_ns_per_image"]
+
+    # ---- tuned (headline)
+    timed_steps(args.warmup)
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    t0 = time.perf_counter()
+    t_tu, u_tu, ms_list = timed_steps(args.steps)
+    wall = time.perf_counter() - t0
+    clocks = clk.stop()
+    t_tu_max = max_over_ranks(t_tu, world, dev)
+    u_all = sum_over_ranks(u_tu, world, dev)
+    value = u_all / t_tu_max
+    rep_tuned = L.fr_tuning_report(ctx)
+
+    # ---- e2e: pinned host inputs copied in every step
+    e2e = None
+    if not args.no_e2e:
+        hosts = []
+        for b in range(min(2, NB)):
+            hi = torch.empty_like(batches[b][0], device="cpu").pin_memory()
+            hi.copy_(batches[b][0])
+            hr = torch.empty_like(batches[b][1], device="cpu").pin_memory()
+            hr.copy_(batches[b][1])
+            hosts.append((hi, hr))
+        d_img = torch.empty_like(batches[0][0])
+        d_rot = torch.empty_like(batches[0][1])
+        D = S + 1
+        V = torch.empty(D ** 3, dtype=torch.complex64, device=dev)
+        W = torch.empty(D ** 3, dtype=torch.float32, device=dev)
+        centre = ((S // 2) * D + S // 2) * D + S // 2
+        w_h = torch.zeros(args.steps, dtype=torch.float32).pin_memory()
+        Vh = torch.empty(D ** 3, dtype=torch.complex64).pin_memory()
+        Wh = torch.empty(D ** 3, dtype=torch.float32).pin_memory()
+        L.fr_reset(ctx)
+        for i in range(args.warmup):
+            hi, hr = hosts[i % len(hosts)]
+            d_img.copy_(hi, non_blocking=True)
+            d_rot.copy_(hr, non_blocking=True)
+            L.fr_insert(ctx, d_img, d_rot)
+        torch.cuda.synchronize()
+        barrier(world)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ups = 0
+        for i in range(args.steps):
+            hi, hr = hosts[i % len(hosts)]
+            d_img.copy_(hi, non_blocking=True)
+            d_rot.copy_(hr, non_blocking=True)
+            L.fr_insert(ctx, d_img, d_rot)
+            L.fr_finalize(ctx, V, W)
+            w_h[i:i + 1].copy_(W[centre:centre + 1], non_blocking=True)
+            ups += updates[i % len(hosts)]
+        Vh.copy_(V, non_blocking=True)
+        Wh.copy_(W, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_e2e = max_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev)
+        e2e = {"value": sum_over_ranks(ups, world, dev) / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": img_bytes + rot_bytes, "d2h_bytes_per_step": 4,
+               "d2h_bytes_end": Vh.numel() * 8 + Wh.numel() * 4,
+               "note": "per step: pinned H2D of the batch and its rotations, fr_insert, fr_finalize, "
+                       "D2H of W at the volume centre; at the end: D2H of the full V and W"}
+
+    # ---- roofline of the dominant kernel (the tuned insertion launch)
+    per_launch_s = t_tu / args.steps
+    ups_per_launch = u_tu / args.steps
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    max_mhz = clocks.get("sm_max_mhz") or 2070.0
+    peak_tflops = sms * 128 * 2 * max_mhz * 1e6 / 1e12
+    achieved = FLOPS_PER_UPDATE * ups_per_launch / per_launch_s / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            tj = json.load(open(prof))
+            if tj.get("config") == L.fr_describe_config(best) and tj.get("S") == S and \
+                    tj.get("source_hash") == source_hash():
+                traffic = tj["bytes_per_launch"]
+        except Exception:
+            traffic = None
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops, "traffic": traffic,
+            "kernel": L.fr_describe_config(best), "flops_per_update": FLOPS_PER_UPDATE,
+            "peak_note": f"FP32 FMA peak: {sms} SMs x 128 lanes x 2 flops x {max_mhz:.0f} MHz (max SM clock)",
+            "avg_launch_ms": 1e3 * per_launch_s, "updates_per_launch": ups_per_launch}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        img0, rot0 = batches[0]
+        m = min(n, 2000)
+        imgc = (inputs.half_values(img0[:m]) if f16 else img0[:m]).cpu().numpy()
+        cpu = oracle_sample(S, imgc, rot0[:m].cpu().numpy(), args.cpu_seconds, a)
+
+    rep = rep_tune
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_tu_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": {"workload": workload_name(S, n, args.dtype), "S": S, "n_per_step": n,
+                   "resident_batches": NB, "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": f"inputs larger than L2 ({img_bytes / 1e9:.2f} GB per batch, {NB} batches cycled)"},
+        "untuned": {"value": sum_over_ranks(u_un, world, dev) / t_un, "config": L.fr_describe_config(untuned_cfg)},
+        "tuning": {"inserts": tune_inserts, "evaluated": rep["evaluated"], "space": rep["space_size"],
+                   "best": L.fr_describe_config(best), "best_ns_per_image": rep["best_ns_per_image"],
+                   "space_avg_ns_per_image": space_avg_ns,
+                   "space_avg_value": (ups_per_launch / n) / (space_avg_ns * 1e-9) if space_avg_ns else None,
+                   "overhead_pct": rep["tuning_overhead_pct"],
+                   "tuning_phase_value": u_tune / t_tune},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": args.steps * launches_per_insert(L, best, n),
+        "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
+        "wall_s_timed": wall,
+    }
+    L.fr_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def launches_per_insert(L, cfg, n):
+    d = L.fr_describe_config(cfg)
+    if d.startswith("gather"):
+        return 1
+    sub = int(d.split("sub=")[1].split()[0])
+    return 2 * math.ceil(n / sub)  # scatter + merge per sub-batch
+
+
+def source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1910_08498_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h", ".inc")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

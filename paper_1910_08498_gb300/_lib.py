@@ -1,0 +1,343 @@
+"""ctypes binding of libfr.so (include/fr.h) -- argument marshalling only.
+
+Each ``fr_*`` function here has the name and argument order of the C entry
+point; torch tensors are passed by ``data_ptr()`` and the stream defaults to
+``torch.cuda.current_stream()``.  Every step of the insertion runs in the
+library's CUDA kernels; there is no Python or CPU fallback: if libfr.so is not
+built, loading fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfr.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "fr.h")
+
+FR_OK, FR_ERR_INVALID_ARG, FR_ERR_UNSUPPORTED, FR_ERR_OOM, FR_ERR_CUDA = 0, 1, 2, 3, 4
+FR_ERR_LAUNCH, FR_ERR_DEVICE_ASSERT, FR_ERR_TIMEOUT, FR_ERR_IO, FR_ERR_STATE = 5, 6, 7, 8, 9
+FR_F32, FR_F16 = 0, 1
+FR_SEARCH_EXHAUSTIVE, FR_SEARCH_RANDOM, FR_SEARCH_LEARNED = 0, 1, 2
+MLP_NPARAM = 5313
+
+
+class FrError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = _lib().fr_error_string(status).decode() if _LIB is not None else str(status)
+        super().__init__(f"{where}: {msg} (status {status})")
+        self.status = status
+
+
+class fr_blob(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_float), ("alpha", ctypes.c_float), ("order", ctypes.c_int),
+                ("table_size", ctypes.c_int)]
+
+
+class fr_options(ctypes.Structure):
+    _fields_ = [("tuning", ctypes.c_int), ("search", ctypes.c_int), ("budget", ctypes.c_int),
+                ("steps_per_insert", ctypes.c_int), ("forced_config", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("debug", ctypes.c_int),
+                ("reserved", ctypes.c_int * 8)]
+
+
+class fr_report(ctypes.Structure):
+    _fields_ = [("S", ctypes.c_int), ("n_bucket", ctypes.c_int), ("space_size", ctypes.c_int),
+                ("evaluated", ctypes.c_int), ("tuned", ctypes.c_int),
+                ("best_config", ctypes.c_int), ("last_config", ctypes.c_int),
+                ("launches", ctypes.c_int), ("best_ns_per_image", ctypes.c_double),
+                ("mean_ns_per_image", ctypes.c_double), ("tuning_overhead_pct", ctypes.c_double),
+                ("images", ctypes.c_ulonglong), ("retunes", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"} | {
+            "predicted_best": self.reserved[0]}
+
+
+_LIB = None
+_LOCK = threading.Lock()
+
+
+def declared_symbols(header: str = HEADER) -> list[str]:
+    """Names of the functions include/fr.h declares."""
+    txt = open(header).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(fr_[a-z0-9_]+)\s*\(", txt)))
+
+
+def _lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built: call paper_1910_08498_gb300.build.build() "
+                               "(or __graft_entry__.build()) first; there is no fallback path")
+        L = ctypes.CDLL(LIB_PATH)
+        i, d, vp, f = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_float
+        P = ctypes.POINTER
+        sig = {
+            "fr_create": (i, [i, P(fr_blob), P(vp)]),
+            "fr_destroy": (i, [vp]),
+            "fr_reset": (i, [vp, vp]),
+            "fr_insert": (i, [vp, vp, i, vp, i, vp]),
+            "fr_insert_batched": (i, [P(vp), P(vp), P(i), P(vp), P(i), i, i, vp]),
+            "fr_finalize": (i, [vp, vp, vp, vp]),
+            "fr_retune": (i, [vp, i]),
+            "fr_set_options": (i, [vp, P(fr_options)]),
+            "fr_get_options": (i, [vp, P(fr_options)]),
+            "fr_tuning_report": (i, [vp, P(fr_report)]),
+            "fr_tuning_save": (i, [vp, ctypes.c_char_p]),
+            "fr_tuning_load": (i, [vp, ctypes.c_char_p]),
+            "fr_num_configs": (i, []),
+            "fr_describe_config": (i, [i, ctypes.c_char_p, i]),
+            "fr_config_valid": (i, [vp, i]),
+            "fr_config_features": (i, [i, i, i, f, P(f)]),
+            "fr_count_updates": (i, [vp, vp, i, vp, P(ctypes.c_ulonglong)]),
+            "fr_relative_performance": (d, [d, d, d, d]),
+            "fr_invocations_to_amortize": (d, [d, d, d, d]),
+            "fr_random_search_steps": (d, [d, d]),
+            "fr_error_string": (ctypes.c_char_p, [i]),
+            "fr_last_device_error": (i, [vp]),
+            "fr_last_cuda_error": (i, []),
+            "fr_debug_fold": (i, [vp, vp, i, vp, vp]),
+            "fr_debug_blob": (i, [vp, vp, i, i, vp, vp]),
+            "fr_mlp_num_params": (i, []),
+            "fr_mlp_forward": (i, [vp, vp, i, vp, vp]),
+            "fr_mlp_backward": (i, [vp, vp, vp, i, vp, vp, vp]),
+            "fr_mlp_adam": (i, [vp, vp, vp, vp, i, f, f, f, f, vp]),
+            "fr_mlp_train": (i, [vp, P(f), P(f), i, i, f, ctypes.c_uint64, P(f)]),
+            "fr_mlp_get": (i, [vp, P(f)]),
+            "fr_mlp_set": (i, [vp, P(f)]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+        return L
+
+
+def lib():
+    """The loaded ctypes library (raises if it is not built)."""
+    return _lib()
+
+
+def _check(rc: int, where: str, ok=(FR_OK,)):
+    if rc not in ok:
+        raise FrError(rc, where)
+    return rc
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _dtype_of(images):
+    import torch
+    if images.dtype in (torch.complex64, torch.float32):
+        return FR_F32
+    if images.dtype == torch.float16:
+        return FR_F16
+    raise TypeError(f"images must be complex64/float32 or float16 (got {images.dtype})")
+
+
+# ------------------------------------------------------------------ C entry points
+
+def fr_create(S: int, a: float = 1.9, alpha: float = 15.0, order: int = 0, table_size: int = 10000):
+    h = ctypes.c_void_p()
+    b = fr_blob(a, alpha, order, table_size)
+    _check(_lib().fr_create(S, ctypes.byref(b), ctypes.byref(h)), "fr_create")
+    return h
+
+
+def fr_destroy(ctx):
+    return _check(_lib().fr_destroy(ctx), "fr_destroy")
+
+
+def fr_reset(ctx, stream=None):
+    return _check(_lib().fr_reset(ctx, _stream(stream)), "fr_reset")
+
+
+def fr_insert(ctx, images, rotations, n: int | None = None, stream=None, allow_fallback=True):
+    """images: CUDA tensor [n,S,S/2+1] complex64 (or [...,2] float32, or [...,2]
+    float16); rotations: CUDA float32 [n,3,3].  Returns the status (FR_OK or
+    FR_ERR_LAUNCH when a configuration was replaced by the fallback)."""
+    if n is None:
+        n = rotations.shape[0]
+    assert images.is_cuda and rotations.is_cuda and images.is_contiguous() and rotations.is_contiguous()
+    ok = (FR_OK, FR_ERR_LAUNCH) if allow_fallback else (FR_OK,)
+    return _check(_lib().fr_insert(ctx, _ptr(images), _dtype_of(images), _ptr(rotations), int(n),
+                                   _stream(stream)), "fr_insert", ok)
+
+
+def fr_insert_batched(ctxs, images, rotations, ns=None, capture=0, stream=None):
+    nb = len(ctxs)
+    if ns is None:
+        ns = [r.shape[0] for r in rotations]
+    C = (ctypes.c_void_p * nb)(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    I = (ctypes.c_void_p * nb)(*[t.data_ptr() for t in images])
+    R = (ctypes.c_void_p * nb)(*[t.data_ptr() for t in rotations])
+    D = (ctypes.c_int * nb)(*[_dtype_of(t) for t in images])
+    N = (ctypes.c_int * nb)(*[int(x) for x in ns])
+    return _check(_lib().fr_insert_batched(C, I, D, R, N, nb, int(capture), _stream(stream)),
+                  "fr_insert_batched")
+
+
+def fr_finalize(ctx, V, W, stream=None):
+    return _check(_lib().fr_finalize(ctx, _ptr(V), _ptr(W), _stream(stream)), "fr_finalize")
+
+
+def fr_retune(ctx, all: bool = False):
+    return _check(_lib().fr_retune(ctx, int(bool(all))), "fr_retune")
+
+
+def fr_get_options(ctx) -> fr_options:
+    o = fr_options()
+    _check(_lib().fr_get_options(ctx, ctypes.byref(o)), "fr_get_options")
+    return o
+
+
+def fr_set_options(ctx, opt: fr_options | None = None, **kw):
+    o = opt if opt is not None else fr_get_options(ctx)
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return _check(_lib().fr_set_options(ctx, ctypes.byref(o)), "fr_set_options")
+
+
+def fr_tuning_report(ctx) -> dict:
+    r = fr_report()
+    _check(_lib().fr_tuning_report(ctx, ctypes.byref(r)), "fr_tuning_report")
+    return r.as_dict()
+
+
+def fr_tuning_save(ctx, path: str):
+    return _check(_lib().fr_tuning_save(ctx, path.encode()), "fr_tuning_save")
+
+
+def fr_tuning_load(ctx, path: str):
+    return _check(_lib().fr_tuning_load(ctx, path.encode()), "fr_tuning_load")
+
+
+def fr_num_configs() -> int:
+    return _lib().fr_num_configs()
+
+
+def fr_describe_config(i: int) -> str:
+    buf = ctypes.create_string_buffer(160)
+    rc = _lib().fr_describe_config(i, buf, 160)
+    if rc < 0:
+        raise FrError(-rc, "fr_describe_config")
+    return buf.value.decode()
+
+
+def fr_config_valid(ctx, i: int) -> bool:
+    return bool(_lib().fr_config_valid(ctx, i))
+
+
+def fr_config_features(i: int, S: int, n: int, a: float):
+    out = (ctypes.c_float * 16)()
+    _check(_lib().fr_config_features(i, S, n, a, out), "fr_config_features")
+    return list(out)
+
+
+def fr_count_updates(ctx, rotations, n=None, stream=None) -> int:
+    if n is None:
+        n = rotations.shape[0]
+    out = ctypes.c_ulonglong(0)
+    _check(_lib().fr_count_updates(ctx, _ptr(rotations), int(n), _stream(stream), ctypes.byref(out)),
+           "fr_count_updates")
+    return int(out.value)
+
+
+def fr_relative_performance(s, t_avg, t_well, n) -> float:
+    return _lib().fr_relative_performance(s, t_avg, t_well, n)
+
+
+def fr_invocations_to_amortize(rp, s, t_avg, t_well) -> float:
+    return _lib().fr_invocations_to_amortize(rp, s, t_avg, t_well)
+
+
+def fr_random_search_steps(r, p) -> float:
+    return _lib().fr_random_search_steps(r, p)
+
+
+def fr_error_string(status: int) -> str:
+    return _lib().fr_error_string(status).decode()
+
+
+def fr_last_device_error(ctx) -> int:
+    return _lib().fr_last_device_error(ctx)
+
+
+def fr_last_cuda_error() -> int:
+    return _lib().fr_last_cuda_error()
+
+
+def fr_debug_fold(r, k, out, stream=None):
+    return _check(_lib().fr_debug_fold(_ptr(r), _ptr(k), out.numel(), _ptr(out), _stream(stream)),
+                  "fr_debug_fold")
+
+
+def fr_debug_blob(ctx, r2, mode, out, stream=None):
+    return _check(_lib().fr_debug_blob(ctx, _ptr(r2), r2.numel(), int(mode), _ptr(out),
+                                       _stream(stream)), "fr_debug_blob")
+
+
+def fr_mlp_num_params() -> int:
+    return _lib().fr_mlp_num_params()
+
+
+def fr_mlp_forward(params, x, y, stream=None):
+    return _check(_lib().fr_mlp_forward(_ptr(params), _ptr(x), x.shape[0], _ptr(y), _stream(stream)),
+                  "fr_mlp_forward")
+
+
+def fr_mlp_backward(params, x, target, grad, loss, stream=None):
+    return _check(_lib().fr_mlp_backward(_ptr(params), _ptr(x), _ptr(target), x.shape[0],
+                                         _ptr(grad), _ptr(loss), _stream(stream)), "fr_mlp_backward")
+
+
+def fr_mlp_adam(params, grad, m1, m2, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    return _check(_lib().fr_mlp_adam(_ptr(params), _ptr(grad), _ptr(m1), _ptr(m2), int(t), lr,
+                                     beta1, beta2, eps, _stream(stream)), "fr_mlp_adam")
+
+
+def fr_mlp_train(ctx, feat, logt, epochs=2000, lr=3e-3, seed=1) -> float:
+    import numpy as np
+    f = np.ascontiguousarray(np.asarray(feat, dtype=np.float32))
+    t = np.ascontiguousarray(np.asarray(logt, dtype=np.float32))
+    m = t.shape[0]
+    assert f.shape == (m, 16)
+    loss = ctypes.c_float(0)
+    FP = ctypes.POINTER(ctypes.c_float)
+    _check(_lib().fr_mlp_train(ctx, f.ctypes.data_as(FP), t.ctypes.data_as(FP), m, int(epochs),
+                               float(lr), int(seed), ctypes.byref(loss)), "fr_mlp_train")
+    return float(loss.value)
+
+
+def fr_mlp_get(ctx):
+    import numpy as np
+    out = np.zeros(MLP_NPARAM, np.float32)
+    _check(_lib().fr_mlp_get(ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), "fr_mlp_get")
+    return out
+
+
+def fr_mlp_set(ctx, params):
+    import numpy as np
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+    assert p.size == MLP_NPARAM
+    return _check(_lib().fr_mlp_set(ctx, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+                  "fr_mlp_set")

@@ -1,0 +1,40 @@
+// fr_ctx.h -- the context object behind the opaque fr_ctx handle.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/fr.h"
+#include "fr_internal.h"
+#include "fr_tuner.h"
+
+struct fr_ctx {
+  int S = 0;
+  fr_blob blob{};
+  fr::Geom g{};
+  int device = 0;
+  float *acc = nullptr;
+  size_t plane = 0;
+  float2 *lut = nullptr;
+  int lut_n = 0;
+  float lut_scale = 0.f;
+  float inv_i0a = 0.f, inv_pa = 0.f;
+  float4 *scratch = nullptr;
+  int *d_err = nullptr;
+  unsigned long long *d_count = nullptr;
+  fr_options opt{};
+  cudaStream_t last_stream = nullptr;
+  unsigned long long images = 0;
+  int launches = 0;
+  fr::Tuner tuner;
+  // cost model
+  float *d_mlp = nullptr;
+  bool mlp_trained = false;
+};
+
+
+namespace fr {
+int key_bucket(int n);
+InsertArgs base_args(const fr_ctx *c);
+int do_insert_ctx(fr_ctx *c, const void *images, fr_dtype dtype, const float *rot, int n,
+                  cudaStream_t st);
+}  // namespace fr

@@ -1,0 +1,58 @@
+// fr_gather_common.cu -- shape table, shared-memory sizing and dispatch of
+// the gather kernel family.
+#include "fr_gather.cuh"
+#include "fr_gather_shapes.h"
+
+namespace fr {
+
+#define FR_DECL(id, bx, by, zc)                                                             \
+  cudaError_t launch_gather_shape##id##_kb4(int wmode, const InsertArgs &a, cudaStream_t st, \
+                                            int query_only, KernelInfo *info);              \
+  cudaError_t launch_gather_shape##id##_kb6(int wmode, const InsertArgs &a, cudaStream_t st, \
+                                            int query_only, KernelInfo *info);
+FR_GATHER_SHAPES(FR_DECL)
+#undef FR_DECL
+
+int num_gather_shapes() { return FR_NUM_GATHER_SHAPES; }
+
+GatherShape gather_shape(int id) {
+#define FR_CASE(i, bx, by, zc) \
+  if (id == i) return GatherShape{bx, by, zc};
+  FR_GATHER_SHAPES(FR_CASE)
+#undef FR_CASE
+  return GatherShape{0, 0, 0};
+}
+
+static size_t up16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+size_t gather_smem_bytes(const GatherShape &sh, int wmode, int lut_n, int pw_max, int tdepth,
+                         int chunk) {
+  (void)sh;
+  size_t b = 0;
+  if (wmode == W_LUT) b += up16((size_t)lut_n * sizeof(float2));
+  b += up16((size_t)chunk * sizeof(int));
+  b += up16((size_t)tdepth * sizeof(SlotParam));
+  size_t cells = (size_t)pw_max * pw_max;
+  b += (size_t)tdepth * cells * sizeof(float2);
+  b += (size_t)tdepth * cells * sizeof(float);
+  return b;
+}
+
+int gather_pw_max(const GatherShape &sh, float a, int KB) {
+  return gather_pw_bound(sh.bx, sh.by, sh.zc, a, KB);
+}
+
+cudaError_t launch_gather(int shape_id, int wmode, const InsertArgs &a, cudaStream_t st,
+                          int query_only, KernelInfo *info) {
+  switch (shape_id) {
+#define FR_SW(i, bx, by, zc)                                                   \
+  case i:                                                                      \
+    return a.g.KB == 4 ? launch_gather_shape##i##_kb4(wmode, a, st, query_only, info) \
+                       : launch_gather_shape##i##_kb6(wmode, a, st, query_only, info);
+    FR_GATHER_SHAPES(FR_SW)
+#undef FR_SW
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace fr

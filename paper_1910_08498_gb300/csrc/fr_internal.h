@@ -1,0 +1,105 @@
+// fr_internal.h -- types shared by the kernels and the host runtime of libfr.
+//
+// Accumulator layout in HBM.  Folding puts every insertion point at q_x >= 0,
+// so a voxel with x < -floor(a) is never touched; the context stores only
+// x in [xa0, S/2] with xa0 = -floor(a).  Six float planes, each
+// [z][y][x - xa0] (x fastest), hold a double-float (hi + lo) running sum of
+// V.re, V.im and W:  plane p at acc + p * plane_elems, order
+// {Vre_hi, Vim_hi, W_hi, Vre_lo, Vim_lo, W_lo}.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace fr {
+
+enum WeightMode { W_LUT = 0, W_OTF = 1 };
+enum Algo { ALGO_GATHER = 0, ALGO_SCATTER = 1 };
+
+struct Geom {
+  int S;      // image side (even)
+  int H;      // S / 2
+  int NX;     // stored columns per row, S / 2 + 1
+  int D;      // volume side, S + 1
+  int xa0;    // first stored accumulator x coordinate, -floor(a)
+  int NXa;    // stored accumulator x extent, H - xa0 + 1
+  float a;    // blob radius
+  float a2;   // a * a
+  float alpha;
+  int KB;     // candidate box width per axis: floor(2a) + 1 rounded up to 4 or 6
+};
+
+// Per-launch arguments of the insertion kernels.
+struct InsertArgs {
+  Geom g;
+  const void *images;   // [n][S][NX] complex, FP32 (float2) or FP16 (half2)
+  int f16;              // 1 if images are FP16
+  const float *rot;     // [n][9]
+  int n;                // images in this launch
+  float *acc;           // 6 planes (see above)
+  size_t plane;         // elements per plane
+  const float2 *lut;    // blob table: (value at node i, value[i+1] - value[i]), lut_n entries
+  int lut_n;
+  float lut_scale;      // (lut_n - 1) / a^2
+  float inv_i0a;        // 1 / I0(alpha) (on-the-fly weights)
+  float inv_pa;         // 1 / (A&S 9.8.2 polynomial at 3.75 / alpha) (on-the-fly weights)
+  int *err;             // device error word
+  // gather geometry
+  int nbx, nby, nbz;    // bricks per axis
+  int pw_max;           // patch side bound (cells)
+  int tdepth;           // images staged per block barrier
+  int chunk;            // images culled per list chunk
+  // scatter
+  float4 *scratch;      // [z][y][x - xa0] (re, im, w, 0)
+};
+
+// Error bits written to the device error word.
+enum DevErr { DERR_RANGE = 1, DERR_TIMEOUT = 2 };
+
+struct KernelInfo {
+  const void *fn;       // __global__ function pointer
+  int threads;          // block size
+  size_t smem;          // dynamic shared memory for the launch
+};
+
+// ---- gather family: template parameters of one instantiation
+struct GatherShape {
+  int bx, by, zc;       // brick: bx x by columns of zc voxels (one column per thread)
+};
+
+// launchers implemented in the .cu files
+cudaError_t launch_gather(int shape_id, int wmode, const InsertArgs &a, cudaStream_t st,
+                          int query_only, KernelInfo *info);
+cudaError_t launch_scatter(int threads, int wmode, const InsertArgs &a, cudaStream_t st,
+                           int query_only, KernelInfo *info);
+cudaError_t launch_merge_scratch(const InsertArgs &a, cudaStream_t st);
+cudaError_t launch_finalize(const Geom &g, const float *acc, size_t plane, float2 *V, float *W,
+                            cudaStream_t st);
+cudaError_t launch_count(const Geom &g, const float *rot, int n, unsigned long long *out,
+                         cudaStream_t st);
+cudaError_t launch_debug_fold(const float *r, const int *k, int m, int *out, cudaStream_t st);
+cudaError_t launch_debug_blob(const InsertArgs &a, const float *r2, int m, int mode, float *out,
+                              cudaStream_t st);
+
+// number of gather shapes and their geometry
+int num_gather_shapes();
+GatherShape gather_shape(int id);
+// dynamic shared memory a gather launch needs
+size_t gather_smem_bytes(const GatherShape &sh, int wmode, int lut_n, int pw_max, int tdepth,
+                         int chunk);
+int gather_pw_max(const GatherShape &sh, float a, int KB);
+
+// MLP kernels
+cudaError_t mlp_forward(const float *params, const float *x, int m, float *y, cudaStream_t st);
+cudaError_t mlp_backward(const float *params, const float *x, const float *t, int m, float *grad,
+                         float *loss, float *work, cudaStream_t st);
+cudaError_t mlp_adam(float *params, const float *grad, float *m1, float *m2, int t, float lr,
+                     float b1, float b2, float eps, cudaStream_t st);
+size_t mlp_work_floats(int m);
+
+constexpr int MLP_IN = 16, MLP_H = 64;
+constexpr int MLP_NPARAM = MLP_IN * MLP_H + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1;
+
+}  // namespace fr

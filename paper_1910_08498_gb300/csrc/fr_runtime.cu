@@ -1,0 +1,467 @@
+// fr_runtime.cu -- host runtime of libfr: contexts, the configuration space,
+// the non-blocking dynamic tuner (Sec. 3.2, Sec. 5.3), tuning-cache
+// persistence and the C ABI declared in include/fr.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "../../include/fr.h"
+#include "fr_internal.h"
+#include "fr_ctx.h"
+#include "fr_tuner.h"
+
+using namespace fr;
+
+namespace {
+
+std::atomic<int> g_last_cuda{0};
+
+inline int cuda_fail(cudaError_t e) {
+  g_last_cuda.store((int)e);
+  if (e == cudaErrorMemoryAllocation) return FR_ERR_OOM;
+  return FR_ERR_CUDA;
+}
+
+#define FR_CUDA(call)                         \
+  do {                                        \
+    cudaError_t e_ = (call);                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+// Host evaluation of the A&S 9.8.2 polynomial (same coefficients as the device).
+double as_982_host(double u) {
+  const double c[9] = {0.39894228, 0.01328592, 0.00225319, -0.00157565, 0.00916281,
+                       -0.02057706, 0.02635537, -0.01647633, 0.00392377};
+  double r = c[8];
+  for (int k = 7; k >= 0; --k) r = r * u + c[k];
+  return r;
+}
+
+}  // namespace
+
+namespace fr {
+
+InsertArgs base_args(const fr_ctx *c) {
+  InsertArgs a{};
+  a.g = c->g;
+  a.acc = c->acc;
+  a.plane = c->plane;
+  a.lut = c->lut;
+  a.lut_n = c->lut_n;
+  a.lut_scale = c->lut_scale;
+  a.inv_i0a = c->inv_i0a;
+  a.inv_pa = c->inv_pa;
+  a.err = c->d_err;
+  a.scratch = c->scratch;
+  return a;
+}
+
+static int ensure_scratch(fr_ctx *c) {
+  if (c->scratch) return FR_OK;
+  FR_CUDA(cudaMalloc(&c->scratch, c->plane * sizeof(float4)));
+  FR_CUDA(cudaMemset(c->scratch, 0, c->plane * sizeof(float4)));
+  return FR_OK;
+}
+
+// Fill the launch geometry of configuration `cfg` into `a`.
+static void gather_geometry(const fr_ctx *c, const Config &cfg, InsertArgs &a) {
+  GatherShape sh = gather_shape(cfg.shape);
+  a.pw_max = gather_pw_max(sh, c->g.a, c->g.KB);
+  a.tdepth = cfg.tdepth;
+  a.chunk = 1024;
+  a.nbx = (c->g.NXa + sh.bx - 1) / sh.bx;
+  a.nby = (c->g.D + sh.by - 1) / sh.by;
+  a.nbz = (c->g.D + sh.zc - 1) / sh.zc;
+}
+
+// Enqueue the insertion of n images with configuration id; no timing.
+int run_config(fr_ctx *c, int id, const void *images, int f16, const float *rot, int n,
+               cudaStream_t st) {
+  const Config &cfg = config_space()[id];
+  InsertArgs a = base_args(c);
+  a.images = images;
+  a.f16 = f16;
+  a.rot = rot;
+  a.n = n;
+  if (cfg.algo == ALGO_GATHER) {
+    gather_geometry(c, cfg, a);
+    cudaError_t e = launch_gather(cfg.shape, cfg.wmode, a, st, 0, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return FR_OK;
+  }
+  int rc = ensure_scratch(c);
+  if (rc) return rc;
+  a.scratch = c->scratch;
+  const size_t px = (size_t)c->g.S * c->g.NX;
+  const size_t bytes = f16 ? 4 : 8;
+  for (int off = 0; off < n; off += cfg.sub) {
+    int m = std::min(cfg.sub, n - off);
+    InsertArgs b = a;
+    b.images = (const char *)images + (size_t)off * px * bytes;
+    b.rot = rot + 9 * (size_t)off;
+    b.n = m;
+    cudaError_t e = launch_scatter(cfg.threads, cfg.wmode, b, st, 0, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = launch_merge_scratch(b, st);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  return FR_OK;
+}
+
+int config_valid(const fr_ctx *c, int id) {
+  if (id < 0 || id >= (int)config_space().size()) return 0;
+  const Config &cfg = config_space()[id];
+  int dev = c ? c->device : 0;
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int lut_n = c ? c->lut_n : 10000;
+  if (cfg.algo == ALGO_GATHER) {
+    GatherShape sh = gather_shape(cfg.shape);
+    float a = c ? c->g.a : 1.9f;
+    int KB = c ? c->g.KB : 4;
+    size_t smem = gather_smem_bytes(sh, cfg.wmode, lut_n, gather_pw_max(sh, a, KB), cfg.tdepth, 1024);
+    return optin == 0 || (int)smem <= optin;
+  }
+  size_t smem = cfg.wmode == W_LUT ? (size_t)lut_n * sizeof(float2) : 0;
+  return optin == 0 || (int)smem <= optin;
+}
+
+}  // namespace fr
+
+// ------------------------------------------------------------------ tuner glue
+
+int fr::key_bucket(int n) {
+  int b = 0;
+  while ((2LL << b) <= n) ++b;
+  return b;
+}
+
+int fr::do_insert_ctx(fr_ctx *c, const void *images, fr_dtype dtype, const float *rot, int n,
+                      cudaStream_t st) {
+  const int f16 = dtype == FR_F16;
+  const size_t px_bytes = (size_t)c->g.S * c->g.NX * (f16 ? 4 : 8);
+  TuneKey key{c->S, key_bucket(n), c->g.a, (int)dtype};
+  c->tuner.harvest();
+  KeyState &ks = c->tuner.state(key, c);
+  std::vector<Step> plan;
+  if (c->opt.forced_config >= 0) {
+    plan.push_back(Step{c->opt.forced_config, n, false});
+  } else {
+    plan = c->tuner.plan(ks, n, c->opt);
+  }
+  int status = FR_OK;
+  int off = 0;
+  for (const Step &s : plan) {
+    if (s.images <= 0) continue;
+    const void *img = (const char *)images + (size_t)off * px_bytes;
+    const float *r = rot + 9 * (size_t)off;
+    Timing tm = c->tuner.begin(st);
+    int rc = run_config(c, s.config, img, f16, r, s.images, st);
+    if (rc != FR_OK) {
+      // the configuration could not launch: mark it and redo the work with the default
+      cudaGetLastError();
+      ks.invalid.insert(s.config);
+      int fb = default_config(c);
+      rc = run_config(c, fb, img, f16, r, s.images, st);
+      if (rc != FR_OK) { c->tuner.abandon(tm); return rc; }
+      c->tuner.end(tm, ks, fb, s.images, false, st);
+      status = FR_ERR_LAUNCH;
+    } else {
+      c->tuner.end(tm, ks, s.config, s.images, s.tuning, st);
+    }
+    ks.last_config = s.config;
+    off += s.images;
+    ++c->launches;
+    if (c->opt.debug) {
+      FR_CUDA(cudaStreamSynchronize(st));
+      int h = 0;
+      FR_CUDA(cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+      if (h) return (h & DERR_TIMEOUT) ? FR_ERR_TIMEOUT : FR_ERR_DEVICE_ASSERT;
+    }
+  }
+  c->images += (unsigned long long)n;
+  c->last_stream = st;
+  return status;
+}
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+int fr_create(int S, const fr_blob *blob, fr_ctx **out) {
+  if (!out) return FR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!blob) return FR_ERR_INVALID_ARG;
+  if (S < 8 || S > 512) return FR_ERR_INVALID_ARG;
+  if (S & 1) return FR_ERR_UNSUPPORTED;
+  if (blob->order != 0) return FR_ERR_UNSUPPORTED;
+  if (!(blob->a > 0.f)) return FR_ERR_INVALID_ARG;
+  if (!(blob->a < 3.f)) return FR_ERR_UNSUPPORTED;
+  if (!(blob->alpha >= 0.f && blob->alpha <= 40.f)) return FR_ERR_INVALID_ARG;
+  if (blob->table_size < 2 || blob->table_size > 16384) return FR_ERR_INVALID_ARG;
+
+  fr_ctx *c = new (std::nothrow) fr_ctx();
+  if (!c) return FR_ERR_OOM;
+  c->S = S;
+  c->blob = *blob;
+  cudaGetDevice(&c->device);
+  Geom &g = c->g;
+  g.S = S;
+  g.H = S / 2;
+  g.NX = S / 2 + 1;
+  g.D = S + 1;
+  g.a = blob->a;
+  g.a2 = blob->a * blob->a;
+  g.alpha = blob->alpha;
+  g.xa0 = -(int)std::floor(blob->a);
+  g.NXa = g.H - g.xa0 + 1;
+  g.KB = blob->a < 2.0f ? 4 : 6;
+  c->plane = (size_t)g.D * g.D * g.NXa;
+  c->opt.tuning = 1;
+  c->opt.search = FR_SEARCH_EXHAUSTIVE;
+  c->opt.budget = 0;
+  c->opt.steps_per_insert = 4;
+  c->opt.forced_config = -1;
+  c->opt.seed = 1;
+  c->opt.debug = 0;
+
+  auto fail = [&](int rc) {
+    fr_destroy(c);
+    return rc;
+  };
+  cudaError_t e = cudaMalloc(&c->acc, 6 * c->plane * sizeof(float));
+  if (e != cudaSuccess) return fail(cuda_fail(e));
+  e = cudaMemset(c->acc, 0, 6 * c->plane * sizeof(float));
+  if (e != cudaSuccess) return fail(cuda_fail(e));
+  e = cudaMalloc(&c->d_err, sizeof(int));
+  if (e != cudaSuccess) return fail(cuda_fail(e));
+  cudaMemset(c->d_err, 0, sizeof(int));
+  e = cudaMalloc(&c->d_count, sizeof(unsigned long long));
+  if (e != cudaSuccess) return fail(cuda_fail(e));
+
+  // blob table: b at r^2 = i a^2 / (N - 1), (value, next - value); I0 from the
+  // C++17 special-function library in double precision
+  const int N = blob->table_size;
+  c->lut_n = N;
+  c->lut_scale = (float)((double)(N - 1) / ((double)g.a * (double)g.a));
+  const double a2 = (double)g.a * (double)g.a, alpha = (double)g.alpha;
+  const double i0a = std::cyl_bessel_i(0.0, alpha);
+  std::vector<double> b(N);
+  for (int i = 0; i < N; ++i) {
+    double t = std::max(0.0, 1.0 - ((double)i * a2 / (N - 1)) / a2);
+    b[i] = std::cyl_bessel_i(0.0, alpha * std::sqrt(t)) / i0a;
+  }
+  std::vector<float2> tab(N);
+  for (int i = 0; i < N; ++i) {
+    float v = (float)b[i];
+    float nxt = i + 1 < N ? (float)b[i + 1] : v;
+    tab[i] = make_float2(v, (float)((double)nxt - (double)v));
+  }
+  e = cudaMalloc(&c->lut, N * sizeof(float2));
+  if (e != cudaSuccess) return fail(cuda_fail(e));
+  e = cudaMemcpy(c->lut, tab.data(), N * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(cuda_fail(e));
+  c->inv_i0a = (float)(1.0 / i0a);
+  c->inv_pa = alpha > 3.75 ? (float)(1.0 / as_982_host(3.75 / alpha)) : 1.0f;
+
+  c->tuner.init(c);
+  *out = c;
+  return FR_OK;
+}
+
+int fr_destroy(fr_ctx *c) {
+  if (!c) return FR_OK;
+  cudaDeviceSynchronize();
+  c->tuner.release();
+  cudaFree(c->acc);
+  cudaFree(c->lut);
+  cudaFree(c->scratch);
+  cudaFree(c->d_err);
+  cudaFree(c->d_count);
+  cudaFree(c->d_mlp);
+  delete c;
+  return FR_OK;
+}
+
+int fr_reset(fr_ctx *c, void *stream) {
+  if (!c) return FR_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  FR_CUDA(cudaMemsetAsync(c->acc, 0, 6 * c->plane * sizeof(float), st));
+  c->images = 0;
+  c->last_stream = st;
+  return FR_OK;
+}
+
+int fr_insert(fr_ctx *c, const void *images, fr_dtype dtype, const float *rotations, int n,
+              void *stream) {
+  if (!c) return FR_ERR_INVALID_ARG;
+  if (n < 0 || n > (1 << 24)) return FR_ERR_INVALID_ARG;
+  if (dtype != FR_F32 && dtype != FR_F16) return FR_ERR_INVALID_ARG;
+  if (n == 0) return FR_OK;
+  if (!images || !rotations) return FR_ERR_INVALID_ARG;
+  if (((uintptr_t)images & 15) != 0 || ((uintptr_t)rotations & 3) != 0) return FR_ERR_INVALID_ARG;
+  return do_insert_ctx(c, images, dtype, rotations, n, (cudaStream_t)stream);
+}
+
+int fr_insert_batched(fr_ctx *const *ctxs, const void *const *images, const fr_dtype *dtypes,
+                      const float *const *rotations, const int *n, int nb, int capture,
+                      void *stream) {
+  if (nb < 0 || (nb > 0 && (!ctxs || !images || !dtypes || !rotations || !n)))
+    return FR_ERR_INVALID_ARG;
+  return fr::insert_batched(ctxs, images, (const int *)dtypes, rotations, n, nb, capture,
+                            (cudaStream_t)stream);
+}
+
+int fr_finalize(fr_ctx *c, void *V, float *W, void *stream) {
+  if (!c || !V || !W) return FR_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  FR_CUDA(cudaStreamSynchronize(st));
+  if (c->last_stream && c->last_stream != st) FR_CUDA(cudaStreamSynchronize(c->last_stream));
+  int h = 0;
+  FR_CUDA(cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  cudaError_t e = launch_finalize(c->g, c->acc, c->plane, (float2 *)V, W, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  c->last_stream = st;
+  if (h) return (h & DERR_TIMEOUT) ? FR_ERR_TIMEOUT : FR_ERR_DEVICE_ASSERT;
+  return FR_OK;
+}
+
+int fr_retune(fr_ctx *c, int all) {
+  if (!c) return FR_ERR_INVALID_ARG;
+  c->tuner.harvest();
+  c->tuner.retune(all != 0);
+  return FR_OK;
+}
+
+int fr_set_options(fr_ctx *c, const fr_options *o) {
+  if (!c || !o) return FR_ERR_INVALID_ARG;
+  if (o->search < 0 || o->search > 2 || o->budget < 0 || o->steps_per_insert < 1)
+    return FR_ERR_INVALID_ARG;
+  if (o->forced_config >= (int)config_space().size()) return FR_ERR_INVALID_ARG;
+  if (o->forced_config >= 0 && !config_valid(c, o->forced_config)) return FR_ERR_UNSUPPORTED;
+  bool search_changed = o->search != c->opt.search || o->budget != c->opt.budget ||
+                        o->seed != c->opt.seed;
+  c->opt = *o;
+  if (search_changed) c->tuner.retune(true);
+  return FR_OK;
+}
+
+int fr_get_options(const fr_ctx *c, fr_options *o) {
+  if (!c || !o) return FR_ERR_INVALID_ARG;
+  *o = c->opt;
+  return FR_OK;
+}
+
+int fr_tuning_report(fr_ctx *c, fr_report *r) {
+  if (!c || !r) return FR_ERR_INVALID_ARG;
+  c->tuner.harvest();
+  std::memset(r, 0, sizeof(*r));
+  c->tuner.report(r);
+  r->S = c->S;
+  r->launches = c->launches;
+  r->images = c->images;
+  return FR_OK;
+}
+
+int fr_tuning_save(const fr_ctx *c, const char *path) {
+  if (!c || !path) return FR_ERR_INVALID_ARG;
+  return const_cast<fr_ctx *>(c)->tuner.save(path);
+}
+
+int fr_tuning_load(fr_ctx *c, const char *path) {
+  if (!c || !path) return FR_ERR_INVALID_ARG;
+  return c->tuner.load(path);
+}
+
+int fr_num_configs(void) { return (int)config_space().size(); }
+
+int fr_describe_config(int id, char *buf, int len) {
+  if (id < 0 || id >= (int)config_space().size() || !buf || len <= 0) return -FR_ERR_INVALID_ARG;
+  std::string s = describe(config_space()[id]);
+  std::snprintf(buf, (size_t)len, "%s", s.c_str());
+  return (int)config_space().size();
+}
+
+int fr_config_valid(const fr_ctx *c, int id) { return config_valid(c, id); }
+
+int fr_config_features(int id, int S, int n, float a, float *out16) {
+  if (id < 0 || id >= (int)config_space().size() || !out16) return FR_ERR_INVALID_ARG;
+  config_features(config_space()[id], S, n, a, out16);
+  return FR_OK;
+}
+
+int fr_count_updates(fr_ctx *c, const float *rot, int n, void *stream, unsigned long long *out) {
+  if (!c || !out || n < 0 || (n > 0 && !rot)) return FR_ERR_INVALID_ARG;
+  *out = 0;
+  if (n == 0) return FR_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  FR_CUDA(cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), st));
+  cudaError_t e = launch_count(c->g, rot, n, c->d_count, st);
+  if (e != cudaSuccess) return cuda_fail(e);
+  FR_CUDA(cudaMemcpyAsync(out, c->d_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  FR_CUDA(cudaStreamSynchronize(st));
+  return FR_OK;
+}
+
+double fr_relative_performance(double s, double t_avg, double t_well, double n) {
+  return relative_performance(s, t_avg, t_well, n);
+}
+double fr_invocations_to_amortize(double rp, double s, double t_avg, double t_well) {
+  return invocations_to_amortize(rp, s, t_avg, t_well);
+}
+double fr_random_search_steps(double r, double p) { return random_search_steps(r, p); }
+
+const char *fr_error_string(int s) {
+  switch (s) {
+    case FR_OK: return "ok";
+    case FR_ERR_INVALID_ARG: return "invalid argument";
+    case FR_ERR_UNSUPPORTED: return "unsupported parameters";
+    case FR_ERR_OOM: return "out of memory";
+    case FR_ERR_CUDA: return "CUDA runtime error";
+    case FR_ERR_LAUNCH: return "configuration failed to launch; work re-run with the fallback";
+    case FR_ERR_DEVICE_ASSERT: return "device range check failed";
+    case FR_ERR_TIMEOUT: return "device wait timed out";
+    case FR_ERR_IO: return "tuning file I/O error";
+    case FR_ERR_STATE: return "invalid state";
+    default: return "unknown status";
+  }
+}
+
+int fr_last_device_error(fr_ctx *c) {
+  if (!c) return FR_ERR_INVALID_ARG;
+  if (c->last_stream) FR_CUDA(cudaStreamSynchronize(c->last_stream));
+  else FR_CUDA(cudaDeviceSynchronize());
+  int h = 0;
+  FR_CUDA(cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  FR_CUDA(cudaMemset(c->d_err, 0, sizeof(int)));
+  if (!h) return FR_OK;
+  return (h & DERR_TIMEOUT) ? FR_ERR_TIMEOUT : FR_ERR_DEVICE_ASSERT;
+}
+
+int fr_last_cuda_error(void) { return g_last_cuda.load(); }
+
+int fr_debug_fold(const float *r, const int *k, int m, int *out, void *stream) {
+  if (m < 0 || (m > 0 && (!r || !k || !out))) return FR_ERR_INVALID_ARG;
+  cudaError_t e = launch_debug_fold(r, k, m, out, (cudaStream_t)stream);
+  return e == cudaSuccess ? FR_OK : cuda_fail(e);
+}
+
+int fr_debug_blob(const fr_ctx *c, const float *r2, int m, int mode, float *out, void *stream) {
+  if (!c || m < 0 || (m > 0 && (!r2 || !out)) || (mode != 0 && mode != 1))
+    return FR_ERR_INVALID_ARG;
+  InsertArgs a = base_args(c);
+  cudaError_t e = launch_debug_blob(a, r2, m, mode, out, (cudaStream_t)stream);
+  return e == cudaSuccess ? FR_OK : cuda_fail(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,437 @@
+// fr_tuner.cu -- configuration space, search orders, event-timed
+// non-blocking tuning steps, amortisation arithmetic and the JSON tuning cache.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <random>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "fr_ctx.h"
+#include "fr_internal.h"
+#include "fr_tuner.h"
+
+namespace fr {
+
+// ------------------------------------------------------------------ space
+//
+// Dimensions (the Fourier row of the paper's tuning space, Sec. 4.2.10,
+// re-derived for this kernel family): algorithm (gather / atomic scatter),
+// brick shape = work-group size and coarsening, image-tile depth (images
+// staged in shared memory per barrier), blob weights from the shared-memory
+// table or on the fly, scatter block size and atomic sub-batch.
+const std::vector<Config> &config_space() {
+  static const std::vector<Config> v = [] {
+    std::vector<Config> c;
+    for (int shape = 0; shape < num_gather_shapes(); ++shape)
+      for (int w : {W_LUT, W_OTF})
+        for (int td : {1, 2, 4, 8}) c.push_back(Config{ALGO_GATHER, shape, w, td, 0, 0});
+    for (int th : {128, 256})
+      for (int w : {W_LUT, W_OTF})
+        for (int sub : {256, 1024}) c.push_back(Config{ALGO_SCATTER, -1, w, 0, th, sub});
+    return c;
+  }();
+  return v;
+}
+
+std::string describe(const Config &c) {
+  char b[128];
+  if (c.algo == ALGO_GATHER) {
+    GatherShape s = gather_shape(c.shape);
+    std::snprintf(b, sizeof b, "gather bx=%d by=%d zc=%d t=%d w=%s", s.bx, s.by, s.zc, c.tdepth,
+                  c.wmode == W_LUT ? "lut" : "otf");
+  } else {
+    std::snprintf(b, sizeof b, "scatter threads=%d sub=%d w=%s", c.threads, c.sub,
+                  c.wmode == W_LUT ? "lut" : "otf");
+  }
+  return b;
+}
+
+unsigned long long space_hash() {
+  unsigned long long h = 1469598103934665603ULL;  // FNV-1a
+  for (const Config &c : config_space())
+    for (char ch : describe(c)) {
+      h ^= (unsigned char)ch;
+      h *= 1099511628211ULL;
+    }
+  return h;
+}
+
+void config_features(const Config &c, int S, int n, float a, float *f) {
+  for (int i = 0; i < 16; ++i) f[i] = 0.f;
+  f[0] = c.algo == ALGO_SCATTER ? 1.f : 0.f;
+  if (c.algo == ALGO_GATHER) {
+    if (c.shape >= 0 && c.shape < 4) f[1 + c.shape] = 1.f;
+    GatherShape s = gather_shape(c.shape);
+    f[6] = std::log2((float)c.tdepth) / 3.f;
+    f[13] = s.zc / 8.f;
+    f[14] = (float)(s.bx * s.by * s.zc) / 2048.f;
+    f[15] = (float)(s.bx * s.by) / 256.f;
+  } else {
+    f[7] = c.threads / 256.f;
+    f[8] = c.sub / 1024.f;
+  }
+  f[5] = c.wmode == W_OTF ? 1.f : 0.f;
+  f[9] = S / 256.f;
+  f[10] = std::log2((float)std::max(n, 1)) / 13.f;
+  f[11] = a / 2.5f;
+  f[12] = (S / 256.f) * (S / 256.f);
+}
+
+int default_config(const fr_ctx *c) {
+  // gather, 16 x 16 x 8 brick, table weights, two images per barrier
+  const auto &sp = config_space();
+  for (int i = 0; i < (int)sp.size(); ++i)
+    if (sp[i].algo == ALGO_GATHER && sp[i].shape == 0 && sp[i].wmode == W_LUT &&
+        sp[i].tdepth == 2 && config_valid(c, i))
+      return i;
+  for (int i = 0; i < (int)sp.size(); ++i)
+    if (config_valid(c, i)) return i;
+  return 0;
+}
+
+// ------------------------------------------------------------------ Sec. 5.4 arithmetic
+
+double relative_performance(double s, double t_avg, double t_well, double n) {
+  return (s * t_avg + (n - s) * t_well) / (n * t_well);
+}
+
+double invocations_to_amortize(double rp, double s, double t_avg, double t_well) {
+  return rp * s * (t_avg / t_well - 1.0) / (1.0 - rp);
+}
+
+double random_search_steps(double r, double p) { return std::log(1.0 - p) / std::log(1.0 - r); }
+
+// ------------------------------------------------------------------ tuner
+
+void Tuner::release() {
+  for (auto &p : pending_) {
+    cudaEventSynchronize(p.t.stop);
+    cudaEventDestroy(p.t.start);
+    cudaEventDestroy(p.t.stop);
+  }
+  pending_.clear();
+  for (cudaEvent_t e : pool_) cudaEventDestroy(e);
+  pool_.clear();
+}
+
+cudaEvent_t Tuner::get_event() {
+  if (!pool_.empty()) {
+    cudaEvent_t e = pool_.back();
+    pool_.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// learned ordering lives in fr_mlp.cu
+std::vector<int> learned_order(fr_ctx *c, const TuneKey &k, const std::vector<int> &valid,
+                               int *predicted_best);
+
+std::vector<int> Tuner::search_order(const TuneKey &k, fr_ctx *c) {
+  std::vector<int> valid;
+  for (int i = 0; i < (int)config_space().size(); ++i)
+    if (config_valid(c, i)) valid.push_back(i);
+  const fr_options &o = c->opt;
+  std::mt19937_64 rng(o.seed ^ ((unsigned long long)k.S << 20) ^ ((unsigned long long)k.nb << 8) ^
+                      (unsigned long long)k.dtype);
+  std::vector<int> order = valid;
+  if (o.search == FR_SEARCH_LEARNED && c->mlp_trained) {
+    int pb = -1;
+    order = learned_order(c, k, valid, &pb);
+    int budget = o.budget > 0 ? o.budget : std::max(1, (int)std::ceil(0.1 * valid.size()));
+    if ((int)order.size() > budget) order.resize(budget);
+    keys_[k].predicted_best = pb;
+    return order;
+  }
+  std::shuffle(order.begin(), order.end(), rng);
+  if (o.search == FR_SEARCH_RANDOM && o.budget > 0 && (int)order.size() > o.budget)
+    order.resize(o.budget);
+  return order;
+}
+
+KeyState &Tuner::state(const TuneKey &k, fr_ctx *c) {
+  auto it = keys_.find(k);
+  if (it == keys_.end()) {
+    KeyState &ks = keys_[k];
+    ks.key = k;
+    ks.order = search_order(k, c);
+    ks.space_size = 0;
+    for (int i = 0; i < (int)config_space().size(); ++i) ks.space_size += config_valid(c, i);
+    if (current_ != nullptr) ++retunes_;
+    current_ = &ks;
+    return ks;
+  }
+  if (current_ != &it->second && current_ != nullptr && !it->second.tuned) ++retunes_;
+  current_ = &it->second;
+  return it->second;
+}
+
+std::vector<Step> Tuner::plan(KeyState &ks, int n, const fr_options &opt) {
+  std::vector<Step> steps;
+  const int fallback = ks.best >= 0 ? ks.best : default_config(ctx_);
+  if (!opt.tuning || ks.tuned) {
+    steps.push_back(Step{fallback, n, false});
+    return steps;
+  }
+  // skip configurations found invalid
+  while (ks.next < ks.order.size() && ks.invalid.count(ks.order[ks.next])) ++ks.next;
+  const int remaining = (int)(ks.order.size() - ks.next);
+  if (remaining <= 0) {
+    steps.push_back(Step{fallback, n, false});
+    return steps;
+  }
+  int k = std::min(std::min(opt.steps_per_insert, remaining), n);
+  int base = n / k, extra = n % k;
+  for (int i = 0; i < k; ++i) {
+    int cfg = ks.order[ks.next++];
+    steps.push_back(Step{cfg, base + (i < extra ? 1 : 0), true});
+  }
+  return steps;
+}
+
+Timing Tuner::begin(cudaStream_t st) {
+  Timing t;
+  t.start = get_event();
+  t.stop = get_event();
+  cudaEventRecord(t.start, st);
+  return t;
+}
+
+void Tuner::end(Timing t, KeyState &ks, int config, int images, bool tuning, cudaStream_t st) {
+  cudaEventRecord(t.stop, st);
+  pending_.push_back(Pending{t, &ks, config, images, tuning});
+  if (tuning) ++ks.pending;
+}
+
+void Tuner::abandon(Timing t) {
+  pool_.push_back(t.start);
+  pool_.push_back(t.stop);
+}
+
+void Tuner::update_best(KeyState &ks) {
+  int best = -1;
+  double bt = 0;
+  for (auto &m : ks.meas) {
+    if (m.second.images <= 0 || ks.invalid.count(m.first)) continue;
+    double t = m.second.per_image();
+    if (best < 0 || t < bt) { best = m.first; bt = t; }
+  }
+  ks.best = best;
+}
+
+void Tuner::finish_if_done(KeyState &ks) {
+  if (!ks.tuned && ks.next >= ks.order.size() && ks.pending == 0) {
+    update_best(ks);
+    ks.tuned = ks.best >= 0;
+  }
+}
+
+void Tuner::harvest() {
+  size_t w = 0;
+  for (size_t i = 0; i < pending_.size(); ++i) {
+    Pending &p = pending_[i];
+    cudaError_t q = cudaEventQuery(p.t.stop);
+    if (q == cudaErrorNotReady) {
+      pending_[w++] = p;
+      continue;
+    }
+    float ms = 0.f;
+    if (q == cudaSuccess && cudaEventElapsedTime(&ms, p.t.start, p.t.stop) == cudaSuccess) {
+      double ns = (double)ms * 1e6;
+      p.ks->all_ns += ns;
+      p.ks->all_images += p.images;
+      if (p.tuning) {
+        Meas &m = p.ks->meas[p.config];
+        m.ns += ns;
+        m.images += p.images;
+        m.launches += 1;
+      }
+    } else {
+      cudaGetLastError();
+    }
+    if (p.tuning) --p.ks->pending;
+    pool_.push_back(p.t.start);
+    pool_.push_back(p.t.stop);
+    update_best(*p.ks);
+    finish_if_done(*p.ks);
+  }
+  pending_.resize(w);
+  for (auto &kv : keys_) finish_if_done(kv.second);
+}
+
+void Tuner::retune(bool all) {
+  // keep pending timings consistent: drop those of the keys being forgotten
+  for (auto &p : pending_) {
+    cudaEventSynchronize(p.t.stop);
+    pool_.push_back(p.t.start);
+    pool_.push_back(p.t.stop);
+  }
+  pending_.clear();
+  if (all) {
+    keys_.clear();
+    current_ = nullptr;
+  } else if (current_) {
+    TuneKey k = current_->key;
+    keys_.erase(k);
+    current_ = nullptr;
+  }
+  ++retunes_;
+}
+
+// predicted-best configuration of a learned search, exposed in reserved[0]
+static void reserved_hint(fr_report *r, const KeyState &ks) { r->reserved[0] = ks.predicted_best; }
+
+void Tuner::report(fr_report *r) {
+  r->best_config = -1;
+  r->last_config = -1;
+  r->retunes = retunes_;
+  if (!current_) return;
+  KeyState &ks = *current_;
+  r->n_bucket = ks.key.nb;
+  r->space_size = ks.space_size;
+  r->evaluated = (int)ks.meas.size();
+  r->tuned = ks.tuned ? 1 : 0;
+  r->best_config = ks.best;
+  r->last_config = ks.last_config;
+  if (ks.best >= 0) r->best_ns_per_image = ks.meas[ks.best].per_image();
+  double sum = 0;
+  int cnt = 0;
+  for (auto &m : ks.meas)
+    if (m.second.images > 0) { sum += m.second.per_image(); ++cnt; }
+  r->mean_ns_per_image = cnt ? sum / cnt : 0;
+  if (ks.best >= 0 && ks.all_images > 0 && r->best_ns_per_image > 0) {
+    double rp = ks.all_ns / (ks.all_images * r->best_ns_per_image);
+    r->tuning_overhead_pct = 100.0 * (rp - 1.0);
+  }
+  reserved_hint(r, ks);
+}
+
+// ------------------------------------------------------------------ persistence
+
+static std::string device_name(int dev, int *sms) {
+  cudaDeviceProp p{};
+  if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) {
+    *sms = 0;
+    return "unknown";
+  }
+  *sms = p.multiProcessorCount;
+  return p.name;
+}
+
+int Tuner::save(const char *path) {
+  harvest();
+  int sms = 0;
+  std::string dev = device_name(ctx_->device, &sms);
+  FILE *f = std::fopen(path, "w");
+  if (!f) return FR_ERR_IO;
+  std::fprintf(f, "{\"version\": 1, \"device\": \"%s\", \"sms\": %d, \"space_hash\": \"%016llx\",\n",
+               dev.c_str(), sms, space_hash());
+  std::fprintf(f, " \"entries\": [");
+  bool first = true;
+  for (auto &kv : keys_) {
+    const KeyState &ks = kv.second;
+    if (ks.meas.empty()) continue;
+    std::fprintf(f, "%s\n  {\"S\": %d, \"nb\": %d, \"a\": %.9g, \"dtype\": %d, \"tuned\": %d, "
+                 "\"best\": %d, \"meas\": [", first ? "" : ",", ks.key.S, ks.key.nb,
+                 (double)ks.key.a, ks.key.dtype, ks.tuned ? 1 : 0, ks.best);
+    bool f2 = true;
+    for (auto &m : ks.meas) {
+      std::fprintf(f, "%s[%d, %.6f, %.1f]", f2 ? "" : ", ", m.first, m.second.ns,
+                   m.second.images);
+      f2 = false;
+    }
+    std::fprintf(f, "]}");
+    first = false;
+  }
+  std::fprintf(f, "\n ]}\n");
+  return std::fclose(f) == 0 ? FR_OK : FR_ERR_IO;
+}
+
+// Minimal reader for the format written above.
+static bool read_file(const char *path, std::string &out) {
+  FILE *f = std::fopen(path, "rb");
+  if (!f) return false;
+  char buf[4096];
+  size_t n;
+  while ((n = std::fread(buf, 1, sizeof buf, f)) > 0) out.append(buf, n);
+  std::fclose(f);
+  return true;
+}
+
+static bool find_num(const std::string &s, size_t from, size_t to, const char *key, double *v) {
+  std::string k = std::string("\"") + key + "\":";
+  size_t p = s.find(k, from);
+  if (p == std::string::npos || p >= to) return false;
+  *v = std::strtod(s.c_str() + p + k.size(), nullptr);
+  return true;
+}
+
+int Tuner::load(const char *path) {
+  std::string s;
+  if (!read_file(path, s)) return FR_ERR_IO;
+  int sms = 0;
+  std::string dev = device_name(ctx_->device, &sms);
+  char hash[32];
+  std::snprintf(hash, sizeof hash, "%016llx", space_hash());
+  if (s.find(std::string("\"device\": \"") + dev + "\"") == std::string::npos) return FR_OK;
+  if (s.find(std::string("\"space_hash\": \"") + hash + "\"") == std::string::npos) return FR_OK;
+  double v = 0;
+  if (!find_num(s, 0, s.size(), "sms", &v) || (int)v != sms) return FR_OK;
+  size_t pos = s.find("\"entries\"");
+  if (pos == std::string::npos) return FR_ERR_IO;
+  while (true) {
+    size_t b = s.find("{\"S\":", pos);
+    if (b == std::string::npos) break;
+    size_t e = s.find("]}", b);
+    if (e == std::string::npos) return FR_ERR_IO;
+    double S, nb, a, dt, tuned, best;
+    if (!find_num(s, b, e, "S", &S) || !find_num(s, b, e, "nb", &nb) ||
+        !find_num(s, b, e, "a", &a) || !find_num(s, b, e, "dtype", &dt) ||
+        !find_num(s, b, e, "tuned", &tuned) || !find_num(s, b, e, "best", &best))
+      return FR_ERR_IO;
+    TuneKey k{(int)S, (int)nb, (float)a, (int)dt};
+    KeyState &ks = keys_[k];
+    ks = KeyState();
+    ks.key = k;
+    ks.space_size = 0;
+    for (int i = 0; i < (int)config_space().size(); ++i) ks.space_size += config_valid(ctx_, i);
+    size_t m = s.find("\"meas\": [", b);
+    size_t p = m + 9;
+    while (p < e) {
+      size_t lb = s.find('[', p);
+      if (lb == std::string::npos || lb >= e) break;
+      char *q = nullptr;
+      int cfg = (int)std::strtol(s.c_str() + lb + 1, &q, 10);
+      double ns = std::strtod(q + 1, &q);
+      double im = std::strtod(q + 1, &q);
+      if (cfg >= 0 && cfg < (int)config_space().size()) {
+        Meas &mm = ks.meas[cfg];
+        mm.ns = ns;
+        mm.images = im;
+        mm.launches = 1;
+      }
+      p = (size_t)(q - s.c_str()) + 1;
+    }
+    // a loaded key is finished if it was finished when saved; otherwise the
+    // unmeasured configurations are searched next
+    std::vector<int> order;
+    for (int i = 0; i < (int)config_space().size(); ++i)
+      if (config_valid(ctx_, i) && !ks.meas.count(i)) order.push_back(i);
+    ks.order = tuned > 0 ? std::vector<int>() : order;
+    ks.next = 0;
+    update_best(ks);
+    ks.tuned = tuned > 0 && ks.best >= 0;
+    pos = e + 2;
+  }
+  return FR_OK;
+}
+
+}  // namespace fr
