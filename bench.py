@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--seed", type=int, default=5)
+    p.add_argument("--profile-config", type=int, default=None,
+                   help="profiling mode: time only this configuration id (no tuning, no baselines)")
     return p.parse_args()
 
 
@@ -296,6 +298,7 @@ def run_ours(args):
         if rep["tuned"] or tune_inserts >= 200:
             break
     rep_tune = L.fr_tuning_report(ctx)
+    meas = L.fr_tuning_measurements(ctx)
     best = rep_tune["best_config"]
     space_avg_ns = rep_tune["mean_ns_per_image"]
 
@@ -409,7 +412,9 @@ def run_ours(args):
                    "space_avg_ns_per_image": space_avg_ns,
                    "space_avg_value": (ups_per_launch / n) / (space_avg_ns * 1e-9) if space_avg_ns else None,
                    "overhead_pct": rep["tuning_overhead_pct"],
-                   "tuning_phase_value": u_tune / t_tune},
+                   "tuning_phase_value": u_tune / t_tune,
+                   "per_config_ns_per_image": {L.fr_describe_config(c): round(ns, 1)
+                                               for c, ns, _ in sorted(meas, key=lambda x: x[1])}},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -444,8 +449,41 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
+def run_profile(args):
+    """Small-case mode for ncu: warm-up then `steps` launches of one configuration."""
+    import numpy as np
+    import torch
+
+    from paper_1910_08498_gb300 import _lib as L
+    from paper_1910_08498_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    img, rot = inputs.make_batch(args.S, args.n, args.seed, device=dev)
+    if args.dtype == "f16":
+        img = inputs.to_half(img)
+    ctx = L.fr_create(args.S, float(np.float32(1.9)), 15.0, 0, 10000)
+    L.fr_set_options(ctx, tuning=0, forced_config=args.profile_config)
+    ups = L.fr_count_updates(ctx, rot)
+    for _ in range(args.warmup):
+        L.fr_insert(ctx, img, rot)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(args.steps):
+        L.fr_insert(ctx, img, rot)
+    e.record()
+    torch.cuda.synchronize()
+    ms = s.elapsed_time(e) / args.steps
+    print(json.dumps({"config": L.fr_describe_config(args.profile_config), "S": args.S, "n": args.n,
+                      "ms_per_launch": ms, "updates_per_launch": ups,
+                      "updates_per_s": ups / (ms * 1e-3)}), flush=True)
+    L.fr_destroy(ctx)
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile_config is not None:
+        return run_profile(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -177,6 +177,12 @@ int fr_get_options(const fr_ctx *ctx, fr_options *opt);
  * not block. */
 int fr_tuning_report(fr_ctx *ctx, fr_report *rep);
 
+/* Per-configuration timings of the current key: up to cap entries of
+ * (configuration id, mean ns per image, images timed) into cfg / ns / images
+ * (host arrays).  Returns the number of measured configurations (which may
+ * exceed cap), or a negative fr_status.  Harvests finished timings first. */
+int fr_tuning_measurements(fr_ctx *ctx, int *cfg, double *ns_per_image, double *images, int cap);
+
 /* Persist / restore the tuning cache as JSON keyed by device name, SM count,
  * S, n bucket, a, dtype and the hash of the configuration space. */
 int fr_tuning_save(const fr_ctx *ctx, const char *path);

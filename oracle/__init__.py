@@ -84,6 +84,10 @@ def blob(r: float, a: float = 1.9, alpha: float = 15.0) -> float:
     return _load().fro_blob(float(r), float(a), float(alpha))
 
 
+def blob_r2(r2: float, a: float = 1.9, alpha: float = 15.0) -> float:
+    return _load().fro_blob_r2(float(r2), float(a), float(alpha))
+
+
 def fold(r00: float, r01: float, kx: int, ky: int) -> bool:
     return bool(_load().fro_fold(float(r00), float(r01), int(kx), int(ky)))
 

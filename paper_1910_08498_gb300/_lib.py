@@ -27,6 +27,8 @@ MLP_NPARAM = 5313
 class FrError(RuntimeError):
     def __init__(self, status: int, where: str):
         msg = _lib().fr_error_string(status).decode() if _LIB is not None else str(status)
+        if status in (FR_ERR_CUDA, FR_ERR_OOM) and _LIB is not None:
+            msg += f" [cudaError {_LIB.fr_last_cuda_error()}]"
         super().__init__(f"{where}: {msg} (status {status})")
         self.status = status
 
@@ -90,6 +92,7 @@ def _lib():
             "fr_set_options": (i, [vp, P(fr_options)]),
             "fr_get_options": (i, [vp, P(fr_options)]),
             "fr_tuning_report": (i, [vp, P(fr_report)]),
+            "fr_tuning_measurements": (i, [vp, P(i), P(d), P(d), i]),
             "fr_tuning_save": (i, [vp, ctypes.c_char_p]),
             "fr_tuning_load": (i, [vp, ctypes.c_char_p]),
             "fr_num_configs": (i, []),
@@ -221,6 +224,18 @@ def fr_tuning_report(ctx) -> dict:
     r = fr_report()
     _check(_lib().fr_tuning_report(ctx, ctypes.byref(r)), "fr_tuning_report")
     return r.as_dict()
+
+
+def fr_tuning_measurements(ctx) -> list[tuple[int, float, float]]:
+    """[(config id, ns per image, images timed)] of the current key."""
+    n = _lib().fr_tuning_measurements(ctx, None, None, None, 0)
+    if n < 0:
+        raise FrError(-n, "fr_tuning_measurements")
+    c = (ctypes.c_int * max(n, 1))()
+    t = (ctypes.c_double * max(n, 1))()
+    im = (ctypes.c_double * max(n, 1))()
+    n = _lib().fr_tuning_measurements(ctx, c, t, im, n)
+    return [(c[k], t[k], im[k]) for k in range(n)]
 
 
 def fr_tuning_save(ctx, path: str):

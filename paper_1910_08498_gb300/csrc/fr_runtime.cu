@@ -373,6 +373,12 @@ int fr_tuning_report(fr_ctx *c, fr_report *r) {
   return FR_OK;
 }
 
+int fr_tuning_measurements(fr_ctx *c, int *cfg, double *ns, double *images, int cap) {
+  if (!c || cap < 0) return -FR_ERR_INVALID_ARG;
+  c->tuner.harvest();
+  return c->tuner.measurements(cfg, ns, images, cap);
+}
+
 int fr_tuning_save(const fr_ctx *c, const char *path) {
   if (!c || !path) return FR_ERR_INVALID_ARG;
   return const_cast<fr_ctx *>(c)->tuner.save(path);

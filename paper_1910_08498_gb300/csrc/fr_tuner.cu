@@ -314,6 +314,20 @@ void Tuner::report(fr_report *r) {
   reserved_hint(r, ks);
 }
 
+int Tuner::measurements(int *cfg, double *ns, double *images, int cap) {
+  if (!current_) return 0;
+  int k = 0;
+  for (auto &m : current_->meas) {
+    if (k < cap) {
+      if (cfg) cfg[k] = m.first;
+      if (ns) ns[k] = m.second.per_image();
+      if (images) images[k] = m.second.images;
+    }
+    ++k;
+  }
+  return k;
+}
+
 // ------------------------------------------------------------------ persistence
 
 static std::string device_name(int dev, int *sms) {

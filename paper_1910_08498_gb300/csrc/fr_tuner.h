@@ -109,6 +109,7 @@ class Tuner {
   void harvest();
   void retune(bool all);
   void report(fr_report *r);
+  int measurements(int *cfg, double *ns, double *images, int cap);
   int save(const char *path);
   int load(const char *path);
   int retunes() const { return retunes_; }
