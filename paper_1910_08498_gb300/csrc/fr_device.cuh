@@ -126,22 +126,26 @@ __device__ __forceinline__ float as_982(float u) {  // u = 3.75 / x
 }
 __device__ __forceinline__ float blob_otf(float r2, float inv_a2, float alpha, float inv_i0a,
                                           float inv_pa) {
-  const float s = fmaxf(fmaf(-r2, inv_a2, 1.0f), 1e-30f);
-  const float rs = rsqrtf(s);        // 1 / sqrt(s)
-  const float x = alpha * (s * rs);  // alpha sqrt(s)
+  const float t = r2 * inv_a2;                   // (r/a)^2
+  const float s = fmaxf(1.0f - t, 1e-30f);
+  const float rs = rsqrtf(s);                    // 1 / sqrt(s)
+  const float sq = s * rs;                       // sqrt(s)
+  const float x = alpha * sq;                    // alpha sqrt(s)
   if (x <= 3.75f) {
-    const float t = x * (1.0f / 3.75f);
-    return as_981(t * t) * inv_i0a;
+    const float u = x * (1.0f / 3.75f);
+    return as_981(u * u) * inv_i0a;
   }
-  const float u = (3.75f / alpha) * rs;  // 3.75 / x
+  // x - alpha = -alpha t / (1 + sqrt(s)) has no cancellation, so exp() sees an
+  // argument accurate to a few ulp even when x is close to alpha
+  const float xm = -alpha * t / (1.0f + sq);
   // sqrt(alpha / x) = s^(-1/4) = sqrt(rs)
-  return expf(x - alpha) * sqrtf(rs) * (as_982(u) * inv_pa);
+  return expf(xm) * sqrtf(rs) * (as_982((3.75f / alpha) * rs) * inv_pa);
 }
 
 template <int WMODE>
 __device__ __forceinline__ float blob_w(const float2 *lut, float r2, const InsertArgs &a,
                                         float inv_a2) {
-  if (WMODE == W_LUT) return blob_lut(lut, r2, a.lut_scale);
+  if (WMODE == W_LUT || WMODE == W_LUT_L1) return blob_lut(lut, r2, a.lut_scale);
   return blob_otf(r2, inv_a2, a.g.alpha, a.inv_i0a, a.inv_pa);
 }
 

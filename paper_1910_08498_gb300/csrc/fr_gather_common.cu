@@ -25,22 +25,17 @@ GatherShape gather_shape(int id) {
 
 static size_t up16(size_t b) { return (b + 15) & ~(size_t)15; }
 
-size_t gather_smem_bytes(const GatherShape &sh, int wmode, int lut_n, int pw_max, int tdepth,
-                         int chunk) {
-  (void)sh;
+size_t gather_smem_bytes(const GatherShape &sh, int wmode, int lut_n, int chunk) {
+  const int nw = sh.bx * sh.by / 32, wv = 32 * sh.zc;
   size_t b = 0;
   if (wmode == W_LUT) b += up16((size_t)lut_n * sizeof(float2));
-  b += up16((size_t)chunk * sizeof(int));
-  b += up16((size_t)tdepth * sizeof(SlotParam));
-  size_t cells = (size_t)pw_max * pw_max;
-  b += (size_t)tdepth * cells * sizeof(float2);
-  b += (size_t)tdepth * cells * sizeof(float);
+  b += (size_t)LIST_FIELDS * chunk * 4;             // image list
+  b += (size_t)nw * 3 * wv * 4;                     // warp partial sums
+  b += (size_t)nw * GATHER_QUEUE * 4;               // warp item queues
   return b;
 }
 
-int gather_pw_max(const GatherShape &sh, float a, int KB) {
-  return gather_pw_bound(sh.bx, sh.by, sh.zc, a, KB);
-}
+int gather_queue_len() { return GATHER_QUEUE; }
 
 cudaError_t launch_gather(int shape_id, int wmode, const InsertArgs &a, cudaStream_t st,
                           int query_only, KernelInfo *info) {

@@ -15,7 +15,9 @@
 
 namespace fr {
 
-enum WeightMode { W_LUT = 0, W_OTF = 1 };
+// blob weights: table staged in shared memory, the same table read through
+// L1 from global memory, or evaluated on the fly
+enum WeightMode { W_LUT = 0, W_OTF = 1, W_LUT_L1 = 2 };
 enum Algo { ALGO_GATHER = 0, ALGO_SCATTER = 1 };
 
 struct Geom {
@@ -48,9 +50,7 @@ struct InsertArgs {
   int *err;             // device error word
   // gather geometry
   int nbx, nby, nbz;    // bricks per axis
-  int pw_max;           // patch side bound (cells)
-  int tdepth;           // images staged per block barrier
-  int chunk;            // images culled per list chunk
+  int chunk;            // images culled per list chunk (images per CTA barrier)
   // scatter
   float4 *scratch;      // [z][y][x - xa0] (re, im, w, 0)
 };
@@ -87,9 +87,8 @@ cudaError_t launch_debug_blob(const InsertArgs &a, const float *r2, int m, int m
 int num_gather_shapes();
 GatherShape gather_shape(int id);
 // dynamic shared memory a gather launch needs
-size_t gather_smem_bytes(const GatherShape &sh, int wmode, int lut_n, int pw_max, int tdepth,
-                         int chunk);
-int gather_pw_max(const GatherShape &sh, float a, int KB);
+size_t gather_smem_bytes(const GatherShape &sh, int wmode, int lut_n, int chunk);
+int gather_queue_len();
 
 // MLP kernels
 cudaError_t mlp_forward(const float *params, const float *x, int m, float *y, cudaStream_t st);

@@ -76,9 +76,7 @@ static int ensure_scratch(fr_ctx *c) {
 // Fill the launch geometry of configuration `cfg` into `a`.
 static void gather_geometry(const fr_ctx *c, const Config &cfg, InsertArgs &a) {
   GatherShape sh = gather_shape(cfg.shape);
-  a.pw_max = gather_pw_max(sh, c->g.a, c->g.KB);
-  a.tdepth = cfg.tdepth;
-  a.chunk = 1024;
+  a.chunk = cfg.chunk;
   a.nbx = (c->g.NXa + sh.bx - 1) / sh.bx;
   a.nby = (c->g.D + sh.by - 1) / sh.by;
   a.nbz = (c->g.D + sh.zc - 1) / sh.zc;
@@ -127,9 +125,7 @@ int config_valid(const fr_ctx *c, int id) {
   int lut_n = c ? c->lut_n : 10000;
   if (cfg.algo == ALGO_GATHER) {
     GatherShape sh = gather_shape(cfg.shape);
-    float a = c ? c->g.a : 1.9f;
-    int KB = c ? c->g.KB : 4;
-    size_t smem = gather_smem_bytes(sh, cfg.wmode, lut_n, gather_pw_max(sh, a, KB), cfg.tdepth, 1024);
+    size_t smem = gather_smem_bytes(sh, cfg.wmode, lut_n, cfg.chunk) + 1024;
     return optin == 0 || (int)smem <= optin;
   }
   size_t smem = cfg.wmode == W_LUT ? (size_t)lut_n * sizeof(float2) : 0;

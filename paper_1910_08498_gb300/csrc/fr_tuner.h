@@ -32,7 +32,7 @@ struct Config {
   int algo;     // ALGO_GATHER or ALGO_SCATTER
   int shape;    // gather brick shape id
   int wmode;    // W_LUT or W_OTF
-  int tdepth;   // gather: images staged per barrier
+  int chunk;    // gather: images culled into the shared-memory list per CTA barrier
   int threads;  // scatter: block size
   int sub;      // scatter: images per atomic sub-batch (merged after each)
 };

@@ -68,11 +68,12 @@ def test_relative_performance_consistent_with_invocations(lib):
 
 def test_configuration_space(lib):
     n = L.fr_num_configs()
-    assert n == 40
+    assert n == 44
     descs = [L.fr_describe_config(i) for i in range(n)]
     assert len(set(descs)) == n
-    assert sum(d.startswith("gather") for d in descs) == 32
-    assert sum("w=otf" in d for d in descs) == 20
+    assert sum(d.startswith("gather") for d in descs) == 36
+    assert sum("w=otf" in d for d in descs) == 16
+    assert sum("w=lut-l1" in d for d in descs) == 12
     with pytest.raises(L.FrError):
         L.fr_describe_config(n)
 
