@@ -1,22 +1,23 @@
 // fr_gather.cuh -- the per-voxel gather insertion kernel (primary variant).
 //
-// One CTA owns a brick of BX x BY voxel columns, ZC voxels deep along z, in
-// the half volume x >= -floor(a) that folding can reach; each warp owns an
-// 8 x 4-column footprint of it (32 * ZC voxels) and is the only writer of
-// those voxels for the whole launch, so V and W in HBM need no atomics.
+// The volume half x >= -floor(a) that folding can reach is cut into warp
+// footprints of 8 x 4 voxel columns, ZC voxels deep; a CTA groups BX/8 x BY/4
+// footprints (and shares the blob table in shared memory).  Each warp is the
+// only writer of its footprint's voxels for the whole launch, so V and W in
+// HBM need no atomics, and warps never wait for one another.
 //
-// Per launch, for each chunk of images:
-//  1. cull (A2): the CTA keeps, in image order, the images whose central
-//     plane passes within a + (brick radius) of the brick centre, compacted
-//     with warp ballots into a shared-memory list (structure of arrays) that
-//     holds each kept image's plane basis and the brick centre's projection
-//     R^T c, formed with error-free products and split into an integer part
-//     and a small remainder so in-plane positions keep ~1e-7 absolute accuracy
-//     at any |k|;
-//  2. queue: each warp walks the list; for an image whose plane passes near
-//     its footprint it marks the voxels within a of the plane (|u_z| <= a,
-//     u = R^T v) and appends them, as (image, voxel) items, to a warp-private
-//     shared-memory queue (warp prefix sums, image-major order);
+// Per warp and launch:
+//  1. cull (A2): one image per lane; an image is kept if its central plane
+//     passes within a + (footprint radius) of the footprint centre and its
+//     extended plane reaches the footprint.  Kept images go, in order, to a
+//     warp-private shared-memory list (structure of arrays) holding the plane
+//     basis and the footprint centre's projection R^T c, formed with error-free
+//     products and split into an integer part and a small remainder so that
+//     in-plane positions keep ~1e-7 absolute accuracy at any |k|;
+//  2. queue: for each list image the warp marks the voxels within a of the
+//     plane (|u_z| <= a, u = R^T v) whose projection lies within the extended
+//     plane [-S/2-a, S/2+a]^2, and appends them, as (image, voxel) items, to a
+//     warp-private queue (warp prefix sums, image-major order);
 //  3. accumulate (A4): all 32 lanes drain the queue, one item per lane, so no
 //     lane idles on a voxel that is far from the plane.  An item visits the
 //     KB x KB pixel box around (u_x, u_y) of the Hermitian-extended, folded
@@ -59,6 +60,11 @@ __device__ __forceinline__ void dot3_dd(float e0, float e1, float e2, float c0, 
   two_sum(p0, p1, s, t1);
   two_sum(s, p2, hi, t2);
   lo = (q0 + q1 + q2) + (t1 + t2);
+}
+
+// true if any column of the 8 x 4 footprint starting at (fx0, fy0) is inside the volume
+__device__ __forceinline__ bool col_in_any(const Geom &g, int fx0, int fy0) {
+  return fx0 <= g.H && fy0 <= g.H;
 }
 
 constexpr int GATHER_FLUSH = 256;  // list images between flushes of the shared partial sums
@@ -109,8 +115,8 @@ template <int WMODE, int KB, int F16>
 __device__ __noinline__ void box_careful(const InsertArgs &args, const float2 *lut,
                                          const unsigned char *ibase, float r00, float r01,
                                          int kx0, int ky0, float fx, float fy, float uz2,
-                                         bool fold_check, float inv_a2, float &sr, float &si,
-                                         float &sw) {
+                                         bool fold_check, float vr2, float inv_a2, float &sr,
+                                         float &si, float &sw) {
   const Geom &g = args.g;
   constexpr int ESZ = F16 ? 4 : 8;
   for (int l = 0; l < KB; ++l) {
@@ -118,10 +124,13 @@ __device__ __noinline__ void box_careful(const InsertArgs &args, const float2 *l
     const float ry = fmaf(dy, dy, uz2);
     const int cy = ky0 + l;
     for (int j = 0; j < KB; ++j) {
-      const float dx = fx - (float)j;
-      const float r2 = fmaf(dx, dx, ry);
-      if (!(r2 <= g.a2)) continue;
       const int cx = kx0 + j;
+      const float dx = fx - (float)j;
+      // the DC pixel sits at q = 0 exactly for every rotation: use the exact
+      // |v|^2 so that a lattice voxel at distance exactly a is decided as the
+      // definition decides it
+      const float r2 = (cx == 0 && cy == 0) ? vr2 : fmaf(dx, dx, ry);
+      if (!(r2 <= g.a2)) continue;
       const float w = blob_w<WMODE>(lut, r2, args, inv_a2);
       // stored pixel c, not folded
       if (cx >= 0 && cx <= g.H && cy >= -g.H && cy < g.H &&
@@ -158,47 +167,46 @@ gather_kernel(const InsertArgs args) {
   const Geom &g = args.g;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const int chunk = args.chunk;
+  const int lcap = args.chunk;  // list capacity per warp
 
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned char *sp = smem;
   float2 *s_lut = reinterpret_cast<float2 *>(sp);
   if (WMODE == W_LUT) sp += ((size_t)args.lut_n * sizeof(float2) + 15) & ~(size_t)15;
-  float *s_list = reinterpret_cast<float *>(sp);  // [LIST_FIELDS][chunk]
-  sp += (size_t)LIST_FIELDS * chunk * 4;
-  float *s_acc = reinterpret_cast<float *>(sp) + (size_t)warp * 3 * WV;  // [3][WV] per warp
-  sp += (size_t)NW * 3 * WV * 4;
-  unsigned *s_q = reinterpret_cast<unsigned *>(sp) + (size_t)warp * GATHER_QUEUE;
-  __shared__ int s_wcount[NW];
-  __shared__ int s_nlist;
+  const size_t per_warp = (size_t)LIST_FIELDS * lcap * 4 + (size_t)3 * WV * 4 + GATHER_QUEUE * 4;
+  sp += (size_t)warp * per_warp;
+  float *s_list = reinterpret_cast<float *>(sp);  // [LIST_FIELDS][lcap]
+  float *s_acc = s_list + (size_t)LIST_FIELDS * lcap;   // [3][WV]
+  unsigned *s_q = reinterpret_cast<unsigned *>(s_acc + 3 * WV);
   const float2 *lut = WMODE == W_LUT ? s_lut : args.lut;
-  auto LF = [&](int f, int i) -> float & { return s_list[f * chunk + i]; };
-  auto LI = [&](int f, int i) -> int { return __float_as_int(s_list[f * chunk + i]); };
+  auto LF = [&](int f, int i) -> float & { return s_list[f * lcap + i]; };
+  auto LI = [&](int f, int i) -> int { return __float_as_int(s_list[f * lcap + i]); };
 
-  // brick and warp footprint
+  // this warp's footprint: 8 x 4 columns, ZC deep
   const int wx = warp % (BX / 8), wy = warp / (BX / 8);
-  const int x0 = g.xa0 + blockIdx.x * BX, y0 = -g.H + blockIdx.y * BY, z0 = -g.H + blockIdx.z * ZC;
-  const float cxb = x0 + 0.5f * (BX - 1), cyb = y0 + 0.5f * (BY - 1), czb = z0 + 0.5f * (ZC - 1);
-  const float hxb = 0.5f * (BX - 1), hyb = 0.5f * (BY - 1), hzb = 0.5f * (ZC - 1);
-  const float rb = sqrtf(hxb * hxb + hyb * hyb + hzb * hzb);
+  const int fx0 = g.xa0 + blockIdx.x * BX + wx * 8;
+  const int fy0 = -g.H + blockIdx.y * BY + wy * 4;
+  const int z0 = -g.H + blockIdx.z * ZC;
+  const float cx = fx0 + 3.5f, cy = fy0 + 1.5f, cz = z0 + 0.5f * (ZC - 1);  // footprint centre
+  const float hz = 0.5f * (ZC - 1);
+  const float rw = sqrtf(3.5f * 3.5f + 1.5f * 1.5f + hz * hz);
   const float a = g.a;
   const float inv_a2 = 1.0f / g.a2;
-  const float cull = a + rb + 1e-3f;
-  const float ext = (float)g.H + rb + a + 1.0f;  // the extended plane spans [-H, H]^2
-  // this lane's column and the warp footprint centre, relative to the brick centre
-  const int tx = wx * 8 + (lane & 7), ty = wy * 4 + (lane >> 3);
-  const int vx = x0 + tx, vy = y0 + ty;
-  const float dvx = (float)vx - cxb, dvy = (float)vy - cyb;
-  const float wcx = (float)(wx * 8) + 3.5f - hxb, wcy = (float)(wy * 4) + 1.5f - hyb;
-  const float wrad = sqrtf(3.5f * 3.5f + 1.5f * 1.5f + hzb * hzb) + a + 1e-3f;
+  const float cull = a + rw + 1e-3f;
+  const float reach = (float)g.H + a;     // the extended plane spans [-H, H]^2
+  const float ext = reach + rw + 1.0f;
+  const int vx = fx0 + (lane & 7), vy = fy0 + (lane >> 3);
+  const float dvx = (float)vx - cx, dvy = (float)vy - cy;
   const bool col_in = vx <= g.H && vy <= g.H;
   const unsigned char *imgs = reinterpret_cast<const unsigned char *>(args.images);
   const size_t img_stride = (size_t)g.S * g.NX * ESZ;
 
   if (WMODE == W_LUT) {
     for (int i = tid; i < args.lut_n; i += NT) s_lut[i] = args.lut[i];
+    __syncthreads();  // the only CTA-wide barrier: warps run independently from here
   }
   for (int i = lane; i < 3 * WV; i += 32) s_acc[i] = 0.f;
+  __syncwarp();
 
   // fold the warp's shared partial sums into HBM (lane owns its column's voxels)
   auto flush = [&]() {
@@ -229,24 +237,23 @@ gather_kernel(const InsertArgs args) {
     __syncwarp();
   };
 
-  // process every queued item; one item per lane per round
+  // process every queued (image, voxel) item; one item per lane per round
   auto drain = [&](int qlen) {
     __syncwarp();
     for (int k = lane; k < qlen; k += 32) {
       const unsigned it = s_q[k];
       const int li = (int)(it >> 8), src = (int)((it >> 3) & 31), t = (int)(it & 7);
-      const int stx = wx * 8 + (src & 7), sty = wy * 4 + (src >> 3);
-      const float sdx = (float)(x0 + stx) - cxb, sdy = (float)(y0 + sty) - cyb;
-      const float dvz = (float)(z0 + t) - czb;
-      const float uz = fmaf(LF(LF_MZ, li), dvz, fmaf(LF(LF_MY, li), sdy, fmaf(LF(LF_MX, li), sdx, LF(LF_UZ, li))));
-      const float uxr = fmaf(LF(LF_E1Z, li), dvz, fmaf(LF(LF_E1Y, li), sdy, fmaf(LF(LF_E1X, li), sdx, LF(LF_FX, li))));
-      const float uyr = fmaf(LF(LF_E2Z, li), dvz, fmaf(LF(LF_E2Y, li), sdy, fmaf(LF(LF_E2X, li), sdx, LF(LF_FY, li))));
+      const int sx = fx0 + (src & 7), sy = fy0 + (src >> 3), sz = z0 + t;
+      const float sdx = (float)sx - cx, sdy = (float)sy - cy, sdz = (float)sz - cz;
+      const float uz = fmaf(LF(LF_MZ, li), sdz, fmaf(LF(LF_MY, li), sdy, fmaf(LF(LF_MX, li), sdx, LF(LF_UZ, li))));
+      const float uxr = fmaf(LF(LF_E1Z, li), sdz, fmaf(LF(LF_E1Y, li), sdy, fmaf(LF(LF_E1X, li), sdx, LF(LF_FX, li))));
+      const float uyr = fmaf(LF(LF_E2Z, li), sdz, fmaf(LF(LF_E2Y, li), sdy, fmaf(LF(LF_E2X, li), sdx, LF(LF_FY, li))));
       const float ixf = ceilf(uxr - a), iyf = ceilf(uyr - a);
       const float fx = uxr - ixf, fy = uyr - iyf;
       const int kx0 = LI(LF_CIX, li) + (int)ixf, ky0 = LI(LF_CIY, li) + (int)iyf;
       const float uz2 = uz * uz;
       const unsigned char *ibase = imgs + (size_t)LI(LF_IMG, li) * img_stride;
-      const bool fold_vox = (x0 + stx) <= -g.xa0;
+      const bool fold_vox = sx <= -g.xa0;
       float sr = 0.f, si = 0.f, sw = 0.f;
       if (!fold_vox && kx0 >= 1 && kx0 + KB - 1 <= g.H && ky0 >= -g.H && ky0 + KB - 1 < g.H) {
         box_fast<WMODE, KB, F16, 1>(args, lut, ibase, kx0, ky0, fx, fy, uz2, inv_a2, sr, si, sw);
@@ -255,8 +262,9 @@ gather_kernel(const InsertArgs args) {
         box_fast<WMODE, KB, F16, -1>(args, lut, ibase, kx0, ky0, fx, fy, uz2, inv_a2, sr, si, sw);
         si = -si;
       } else {
+        const float vr2 = (float)(sx * sx + sy * sy + sz * sz);
         box_careful<WMODE, KB, F16>(args, lut, ibase, LF(LF_E1X, li), LF(LF_E2X, li), kx0, ky0,
-                                    fx, fy, uz2, fold_vox, inv_a2, sr, si, sw);
+                                    fx, fy, uz2, fold_vox, vr2, inv_a2, sr, si, sw);
       }
       const int slot = src * ZC + t;
       atomicAdd(&s_acc[slot], sr);
@@ -266,105 +274,101 @@ gather_kernel(const InsertArgs args) {
     __syncwarp();
   };
 
-  const float *rot = args.rot;
-  int since_flush = 0;
-  for (int cs = 0; cs < args.n; cs += chunk) {
-    const int ce = min(args.n, cs + chunk);
-    // ---- 1. cull this chunk into an ordered list
-    if (tid == 0) s_nlist = 0;
-    __syncthreads();
-    for (int base = cs; base < ce; base += NT) {
-      const int i = base + tid;
-      bool keep = false;
-      float e1x = 0, e1y = 0, e1z = 0, e2x = 0, e2y = 0, e2z = 0, mx = 0, my = 0, mz = 0;
-      if (i < ce) {
-        const float *R = rot + 9 * (size_t)i;
-        e1x = __ldg(R + 0); e1y = __ldg(R + 3); e1z = __ldg(R + 6);
-        e2x = __ldg(R + 1); e2y = __ldg(R + 4); e2z = __ldg(R + 7);
-        mx = __ldg(R + 2);  my = __ldg(R + 5);  mz = __ldg(R + 8);
-        const float d = mx * cxb + my * cyb + mz * czb;
-        const float ux = e1x * cxb + e1y * cyb + e1z * czb;
-        const float uy = e2x * cxb + e2y * cyb + e2z * czb;
-        keep = fabsf(d) <= cull && fabsf(ux) <= ext && fabsf(uy) <= ext;
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, keep);
-      if (lane == 0) s_wcount[warp] = __popc(bal);
-      __syncthreads();
-      int off = s_nlist;
-      for (int w = 0; w < warp; ++w) off += s_wcount[w];
-      if (keep) {
-        const int o = off + __popc(bal & ((1u << lane) - 1u));
-        float hx, lx, hy, ly, hz, lz;
-        dot3_dd(e1x, e1y, e1z, cxb, cyb, czb, hx, lx);
-        dot3_dd(e2x, e2y, e2z, cxb, cyb, czb, hy, ly);
-        dot3_dd(mx, my, mz, cxb, cyb, czb, hz, lz);
-        const float rx = rintf(hx), ry = rintf(hy);
-        LF(LF_E1X, o) = e1x; LF(LF_E1Y, o) = e1y; LF(LF_E1Z, o) = e1z;
-        LF(LF_E2X, o) = e2x; LF(LF_E2Y, o) = e2y; LF(LF_E2Z, o) = e2z;
-        LF(LF_MX, o) = mx;   LF(LF_MY, o) = my;   LF(LF_MZ, o) = mz;
-        LF(LF_FX, o) = (hx - rx) + lx;  // hx - rx is exact
-        LF(LF_FY, o) = (hy - ry) + ly;
-        LF(LF_UZ, o) = hz + lz;
-        LF(LF_CIX, o) = __int_as_float((int)rx);
-        LF(LF_CIY, o) = __int_as_float((int)ry);
-        LF(LF_IMG, o) = __int_as_float(i);
-      }
-      __syncthreads();
-      if (tid == 0) {
-        int tot = 0;
-        for (int w = 0; w < NW; ++w) tot += s_wcount[w];
-        s_nlist += tot;
-      }
-      __syncthreads();
+  // queue the footprint's voxels near the plane of list entry li and inside
+  // the image's reach; drain when the queue could overflow
+  int qlen = 0;
+  auto enqueue = [&](int li) {
+    const float mx = LF(LF_MX, li), my = LF(LF_MY, li), mz = LF(LF_MZ, li);
+    const float bz = fmaf(my, dvy, fmaf(mx, dvx, LF(LF_UZ, li)));
+    const float bx = fmaf(LF(LF_E1Y, li), dvy, fmaf(LF(LF_E1X, li), dvx, LF(LF_FX, li)));
+    const float by = fmaf(LF(LF_E2Y, li), dvy, fmaf(LF(LF_E2X, li), dvx, LF(LF_FY, li)));
+    const float cix = (float)LI(LF_CIX, li), ciy = (float)LI(LF_CIY, li);
+    const float e1z = LF(LF_E1Z, li), e2z = LF(LF_E2Z, li);
+    unsigned mask = 0;
+#pragma unroll
+    for (int t = 0; t < ZC; ++t) {
+      const float dz = (float)(z0 + t) - cz;
+      const float uz = fmaf(mz, dz, bz);
+      const float ux = cix + fmaf(e1z, dz, bx), uy = ciy + fmaf(e2z, dz, by);
+      const bool hit = fabsf(uz) <= a && fabsf(ux) <= reach && fabsf(uy) <= reach;
+      mask |= (hit ? 1u : 0u) << t;
     }
-    const int nlist = s_nlist;
+    if (!col_in) mask = 0;
+    const int cnt = __popc(mask);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    int pos = qlen + incl - cnt;
+    while (mask) {
+      const int t = __ffs(mask) - 1;
+      mask &= mask - 1;
+      s_q[pos++] = ((unsigned)li << 8) | ((unsigned)lane << 3) | (unsigned)t;
+    }
+    qlen += total;
+    if (qlen > GATHER_QUEUE - WV) {
+      drain(qlen);
+      qlen = 0;
+    }
+  };
 
-    // ---- 2./3. queue the warp's near-plane voxels and drain
-    int qlen = 0;
-    for (int li = 0; li < nlist; ++li) {
-      const float mx = LF(LF_MX, li), my = LF(LF_MY, li), mz = LF(LF_MZ, li);
-      // the plane must pass near this warp's footprint
-      const float dw = fmaf(my, wcy, fmaf(mx, wcx, LF(LF_UZ, li)));
-      if (fabsf(dw) <= wrad) {
-        const float bz = fmaf(my, dvy, fmaf(mx, dvx, LF(LF_UZ, li)));
-        unsigned mask = 0;
-#pragma unroll
-        for (int t = 0; t < ZC; ++t) {
-          const float uz = fmaf(mz, (float)(z0 + t) - czb, bz);
-          mask |= (fabsf(uz) <= a ? 1u : 0u) << t;
-        }
-        if (!col_in) mask = 0;
-        // warp prefix sum of the item counts
-        const int cnt = __popc(mask);
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int v = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += v;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        int pos = qlen + incl - cnt;
-        while (mask) {
-          const int t = __ffs(mask) - 1;
-          mask &= mask - 1;
-          s_q[pos++] = ((unsigned)li << 8) | ((unsigned)lane << 3) | (unsigned)t;
-        }
-        qlen += total;
-        if (qlen > GATHER_QUEUE - WV) {
-          drain(qlen);
-          qlen = 0;
-        }
-      }
+  const float *rot = args.rot;
+  int nl = 0;           // entries in the warp's list
+  int since_flush = 0;  // list entries queued since the last flush
+  auto process_list = [&]() {
+    for (int li = 0; li < nl; ++li) {
+      enqueue(li);
       if (++since_flush >= GATHER_FLUSH) {
         if (qlen) { drain(qlen); qlen = 0; }
         flush();
         since_flush = 0;
       }
     }
-    if (qlen) drain(qlen);
-    __syncthreads();  // the list is rebuilt for the next chunk
+    if (qlen) { drain(qlen); qlen = 0; }
+    nl = 0;
+  };
+
+  // ---- cull: one image per lane; kept images go to the warp's list in order
+  for (int cs = 0; cs < args.n; cs += 32) {
+    const int i = cs + lane;
+    bool keep = false;
+    float e1x = 0, e1y = 0, e1z = 0, e2x = 0, e2y = 0, e2z = 0, mx = 0, my = 0, mz = 0;
+    if (i < args.n) {
+      const float *R = rot + 9 * (size_t)i;
+      e1x = __ldg(R + 0); e1y = __ldg(R + 3); e1z = __ldg(R + 6);
+      e2x = __ldg(R + 1); e2y = __ldg(R + 4); e2z = __ldg(R + 7);
+      mx = __ldg(R + 2);  my = __ldg(R + 5);  mz = __ldg(R + 8);
+      const float d = mx * cx + my * cy + mz * cz;
+      const float ux = e1x * cx + e1y * cy + e1z * cz;
+      const float uy = e2x * cx + e2y * cy + e2z * cz;
+      keep = col_in_any(g, fx0, fy0) && fabsf(d) <= cull && fabsf(ux) <= ext && fabsf(uy) <= ext;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+      const int o = nl + __popc(bal & ((1u << lane) - 1u));
+      float hx, lx, hy, ly, hz2, lz;
+      dot3_dd(e1x, e1y, e1z, cx, cy, cz, hx, lx);
+      dot3_dd(e2x, e2y, e2z, cx, cy, cz, hy, ly);
+      dot3_dd(mx, my, mz, cx, cy, cz, hz2, lz);
+      const float rx = rintf(hx), ry = rintf(hy);
+      LF(LF_E1X, o) = e1x; LF(LF_E1Y, o) = e1y; LF(LF_E1Z, o) = e1z;
+      LF(LF_E2X, o) = e2x; LF(LF_E2Y, o) = e2y; LF(LF_E2Z, o) = e2z;
+      LF(LF_MX, o) = mx;   LF(LF_MY, o) = my;   LF(LF_MZ, o) = mz;
+      LF(LF_FX, o) = (hx - rx) + lx;  // hx - rx is exact
+      LF(LF_FY, o) = (hy - ry) + ly;
+      LF(LF_UZ, o) = hz2 + lz;
+      LF(LF_CIX, o) = __int_as_float((int)rx);
+      LF(LF_CIY, o) = __int_as_float((int)ry);
+      LF(LF_IMG, o) = __int_as_float(i);
+    }
+    nl += __popc(bal);
+    __syncwarp();
+    if (nl > lcap - 32) process_list();
   }
-  // ---- 4. final write back
+  process_list();
   flush();
 }
 

@@ -29,9 +29,8 @@ size_t gather_smem_bytes(const GatherShape &sh, int wmode, int lut_n, int chunk)
   const int nw = sh.bx * sh.by / 32, wv = 32 * sh.zc;
   size_t b = 0;
   if (wmode == W_LUT) b += up16((size_t)lut_n * sizeof(float2));
-  b += (size_t)LIST_FIELDS * chunk * 4;             // image list
-  b += (size_t)nw * 3 * wv * 4;                     // warp partial sums
-  b += (size_t)nw * GATHER_QUEUE * 4;               // warp item queues
+  // per warp: image list, partial sums, item queue
+  b += (size_t)nw * ((size_t)LIST_FIELDS * chunk * 4 + (size_t)3 * wv * 4 + GATHER_QUEUE * 4);
   return b;
 }
 

@@ -30,7 +30,7 @@ const std::vector<Config> &config_space() {
     std::vector<Config> c;
     for (int shape = 0; shape < num_gather_shapes(); ++shape)
       for (int w : {W_LUT, W_LUT_L1, W_OTF})
-        for (int ch : {128, 256, 512}) c.push_back(Config{ALGO_GATHER, shape, w, ch, 0, 0});
+        for (int ch : {64, 128, 256}) c.push_back(Config{ALGO_GATHER, shape, w, ch, 0, 0});
     for (int th : {128, 256})
       for (int w : {W_LUT, W_OTF})
         for (int sub : {256, 1024}) c.push_back(Config{ALGO_SCATTER, -1, w, 0, th, sub});
@@ -68,7 +68,7 @@ void config_features(const Config &c, int S, int n, float a, float *f) {
   if (c.algo == ALGO_GATHER) {
     if (c.shape >= 0 && c.shape < 4) f[1 + c.shape] = 1.f;
     GatherShape s = gather_shape(c.shape);
-    f[6] = std::log2((float)c.chunk / 128.f) / 2.f;
+    f[6] = std::log2((float)c.chunk / 64.f) / 2.f;
     f[13] = s.zc / 8.f;
     f[14] = (float)(s.bx * s.by * s.zc) / 2048.f;
     f[15] = (float)(s.bx * s.by) / 256.f;
@@ -84,11 +84,11 @@ void config_features(const Config &c, int S, int n, float a, float *f) {
 }
 
 int default_config(const fr_ctx *c) {
-  // gather, 16 x 16 x 8 brick, table weights through L1, 256-image list chunks
+  // gather, 16 x 16 x 8 CTA, table weights through L1, 128-image warp lists
   const auto &sp = config_space();
   for (int i = 0; i < (int)sp.size(); ++i)
     if (sp[i].algo == ALGO_GATHER && sp[i].shape == 0 && sp[i].wmode == W_LUT_L1 &&
-        sp[i].chunk == 256 && config_valid(c, i))
+        sp[i].chunk == 128 && config_valid(c, i))
       return i;
   for (int i = 0; i < (int)sp.size(); ++i)
     if (config_valid(c, i)) return i;
