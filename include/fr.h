@@ -232,7 +232,8 @@ int fr_last_cuda_error(void);
 int fr_debug_fold(const float *r, const int *k, int m, int *out, void *stream);
 
 /* Evaluate the device blob weight for m squared distances r2 (device float[m])
- * with the table (mode 0) or on the fly (mode 1) into out (device float[m]). */
+ * into out (device float[m]): mode 0 the table, mode 1 the Abramowitz & Stegun
+ * Bessel approximations, mode 2 the register polynomial.  Test hook. */
 int fr_debug_blob(const fr_ctx *ctx, const float *r2, int m, int mode, float *out, void *stream);
 
 /* ---------------------------------------------------------------- learned tuner */

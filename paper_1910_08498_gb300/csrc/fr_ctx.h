@@ -18,6 +18,8 @@ struct fr_ctx {
   int lut_n = 0;
   float lut_scale = 0.f;
   float inv_i0a = 0.f, inv_pa = 0.f;
+  float poly[fr::POLY_N] = {};
+  double poly_err = 1.0;  // max |poly - b| measured on the host (FP32 Horner)
   float4 *scratch = nullptr;
   int *d_err = nullptr;
   unsigned long long *d_count = nullptr;

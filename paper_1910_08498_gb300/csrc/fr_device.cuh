@@ -142,10 +142,22 @@ __device__ __forceinline__ float blob_otf(float r2, float inv_a2, float alpha, f
   return expf(xm) * sqrtf(rs) * (as_982((3.75f / alpha) * rs) * inv_pa);
 }
 
+// Polynomial blob: b(r) = sum_k c_k x^k, x = 2 r^2 / a^2 - 1, the
+// Chebyshev interpolant of degree 13 converted to the power basis on the host
+// (Horner in FP32; absolute error below 1e-6 for the blobs it is enabled for).
+__device__ __forceinline__ float blob_poly(float r2, float two_inv_a2, const float *c) {
+  const float x = fmaf(r2, two_inv_a2, -1.0f);
+  float p = c[POLY_N - 1];
+#pragma unroll
+  for (int k = POLY_N - 2; k >= 0; --k) p = fmaf(p, x, c[k]);
+  return p;
+}
+
 template <int WMODE>
 __device__ __forceinline__ float blob_w(const float2 *lut, float r2, const InsertArgs &a,
                                         float inv_a2) {
-  if (WMODE == W_LUT || WMODE == W_LUT_L1) return blob_lut(lut, r2, a.lut_scale);
+  if (WMODE == W_LUT) return blob_lut(lut, r2, a.lut_scale);
+  if (WMODE == W_POLY) return blob_poly(r2, 2.0f * inv_a2, a.poly);
   return blob_otf(r2, inv_a2, a.g.alpha, a.inv_i0a, a.inv_pa);
 }
 

@@ -23,7 +23,8 @@
 //     KB x KB pixel box around (u_x, u_y) of the Hermitian-extended, folded
 //     image plane and forms sum b(r) p and sum b(r) over the pixels with
 //     r^2 = (u_x-kx)^2 + (u_y-ky)^2 + u_z^2 <= a^2 (weights from the blob
-//     table in shared memory, the same table through L1, or on the fly).
+//     table in shared memory, or on the fly: a register-held polynomial in
+//     r^2 or the Abramowitz & Stegun Bessel approximations).
 //     Pixels are read through L1; consecutive items are neighbouring voxels of
 //     one image, so their boxes share sectors.  A box wholly in the stored half
 //     plane (kx >= 1) or wholly in its mirror (kx <= -1), inside the image, for
@@ -68,7 +69,7 @@ __device__ __forceinline__ bool col_in_any(const Geom &g, int fx0, int fy0) {
 }
 
 constexpr int GATHER_FLUSH = 256;  // list images between flushes of the shared partial sums
-constexpr int GATHER_QUEUE = 512;  // queue entries per warp
+constexpr int GATHER_QUEUE_SLACK = 64;  // queue entries per warp beyond one image's worth
 
 template <int F16>
 __device__ __forceinline__ float2 ld_px(const unsigned char *p) {
@@ -173,12 +174,13 @@ gather_kernel(const InsertArgs args) {
   unsigned char *sp = smem;
   float2 *s_lut = reinterpret_cast<float2 *>(sp);
   if (WMODE == W_LUT) sp += ((size_t)args.lut_n * sizeof(float2) + 15) & ~(size_t)15;
-  const size_t per_warp = (size_t)LIST_FIELDS * lcap * 4 + (size_t)3 * WV * 4 + GATHER_QUEUE * 4;
+  const size_t per_warp =
+      (size_t)LIST_FIELDS * lcap * 4 + (size_t)3 * WV * 4 + (size_t)(WV + GATHER_QUEUE_SLACK) * 4;
   sp += (size_t)warp * per_warp;
   float *s_list = reinterpret_cast<float *>(sp);  // [LIST_FIELDS][lcap]
   float *s_acc = s_list + (size_t)LIST_FIELDS * lcap;   // [3][WV]
   unsigned *s_q = reinterpret_cast<unsigned *>(s_acc + 3 * WV);
-  const float2 *lut = WMODE == W_LUT ? s_lut : args.lut;
+  const float2 *lut = s_lut;
   auto LF = [&](int f, int i) -> float & { return s_list[f * lcap + i]; };
   auto LI = [&](int f, int i) -> int { return __float_as_int(s_list[f * lcap + i]); };
 
@@ -309,7 +311,7 @@ gather_kernel(const InsertArgs args) {
       s_q[pos++] = ((unsigned)li << 8) | ((unsigned)lane << 3) | (unsigned)t;
     }
     qlen += total;
-    if (qlen > GATHER_QUEUE - WV) {
+    if (qlen > GATHER_QUEUE_SLACK) {
       drain(qlen);
       qlen = 0;
     }

@@ -15,9 +15,11 @@
 
 namespace fr {
 
-// blob weights: table staged in shared memory, the same table read through
-// L1 from global memory, or evaluated on the fly
-enum WeightMode { W_LUT = 0, W_OTF = 1, W_LUT_L1 = 2 };
+// blob weights: table staged in shared memory (precomputed), Abramowitz &
+// Stegun Bessel approximations evaluated per pixel, or a Chebyshev polynomial
+// in r^2 held in registers (both on the fly)
+enum WeightMode { W_LUT = 0, W_OTF = 1, W_POLY = 2 };
+constexpr int POLY_N = 14;  // coefficients of the degree-13 weight polynomial
 enum Algo { ALGO_GATHER = 0, ALGO_SCATTER = 1 };
 
 struct Geom {
@@ -47,6 +49,7 @@ struct InsertArgs {
   float lut_scale;      // (lut_n - 1) / a^2
   float inv_i0a;        // 1 / I0(alpha) (on-the-fly weights)
   float inv_pa;         // 1 / (A&S 9.8.2 polynomial at 3.75 / alpha) (on-the-fly weights)
+  float poly[POLY_N];   // b as a polynomial in x = 2 r^2 / a^2 - 1, power basis (W_POLY)
   int *err;             // device error word
   // gather geometry
   int nbx, nby, nbz;    // bricks per axis

@@ -203,8 +203,10 @@ __global__ void debug_blob_kernel(const InsertArgs args, const float *r2, int m,
   if (i >= m) return;
   float v = r2[i];
   if (!(v >= 0.f && v <= args.g.a2)) { out[i] = 0.f; return; }
+  const float inv_a2 = 1.0f / args.g.a2;
   out[i] = mode == 0 ? blob_lut(args.lut, v, args.lut_scale)
-                     : blob_otf(v, 1.0f / args.g.a2, args.g.alpha, args.inv_i0a, args.inv_pa);
+         : mode == 1 ? blob_otf(v, inv_a2, args.g.alpha, args.inv_i0a, args.inv_pa)
+                     : blob_poly(v, 2.0f * inv_a2, args.poly);
 }
 
 // ---------------------------------------------------------------- launchers

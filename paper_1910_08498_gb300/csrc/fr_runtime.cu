@@ -47,6 +47,33 @@ double as_982_host(double u) {
   return r;
 }
 
+// Chebyshev interpolant of degree POLY_N-1 of f on [-1, 1] at the first-kind
+// nodes x_k = cos((k + 1/2) pi / N) (Mason & Handscomb, Chebyshev Polynomials,
+// 2003, Sec. 6.3: c_j = (2/N) sum_k f(x_k) T_j(x_k), c_0 halved), converted to
+// the power basis with T_{j+1} = 2 x T_j - T_{j-1}.
+template <class F>
+void chebyshev_power_basis(F f, double *mono) {
+  const int N = POLY_N;
+  const double pi = 3.14159265358979323846;
+  double fx[N], cheb[N];
+  for (int k = 0; k < N; ++k) fx[k] = f(std::cos(pi * (k + 0.5) / N));
+  for (int j = 0; j < N; ++j) {
+    double s = 0;
+    for (int k = 0; k < N; ++k) s += fx[k] * std::cos(pi * j * (k + 0.5) / N);
+    cheb[j] = 2.0 * s / N;
+  }
+  cheb[0] *= 0.5;
+  double tprev[N] = {0}, tcur[N] = {0}, tnext[N];
+  tprev[0] = 1.0;  // T_0
+  tcur[1] = 1.0;   // T_1
+  for (int i = 0; i < N; ++i) mono[i] = cheb[0] * tprev[i] + (N > 1 ? cheb[1] * tcur[i] : 0.0);
+  for (int j = 2; j < N; ++j) {
+    for (int i = 0; i < N; ++i) tnext[i] = (i ? 2.0 * tcur[i - 1] : 0.0) - tprev[i];
+    for (int i = 0; i < N; ++i) mono[i] += cheb[j] * tnext[i];
+    for (int i = 0; i < N; ++i) { tprev[i] = tcur[i]; tcur[i] = tnext[i]; }
+  }
+}
+
 }  // namespace
 
 namespace fr {
@@ -61,6 +88,7 @@ InsertArgs base_args(const fr_ctx *c) {
   a.lut_scale = c->lut_scale;
   a.inv_i0a = c->inv_i0a;
   a.inv_pa = c->inv_pa;
+  for (int k = 0; k < POLY_N; ++k) a.poly[k] = c->poly[k];
   a.err = c->d_err;
   a.scratch = c->scratch;
   return a;
@@ -119,6 +147,8 @@ int run_config(fr_ctx *c, int id, const void *images, int f16, const float *rot,
 int config_valid(const fr_ctx *c, int id) {
   if (id < 0 || id >= (int)config_space().size()) return 0;
   const Config &cfg = config_space()[id];
+  // the polynomial is offered only where it is as accurate as the table
+  if (cfg.wmode == W_POLY && c && !(c->poly_err < 1e-6)) return 0;
   int dev = c ? c->device : 0;
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -269,6 +299,26 @@ int fr_create(int S, const fr_blob *blob, fr_ctx **out) {
   if (e != cudaSuccess) return fail(cuda_fail(e));
   c->inv_i0a = (float)(1.0 / i0a);
   c->inv_pa = alpha > 3.75 ? (float)(1.0 / as_982_host(3.75 / alpha)) : 1.0f;
+
+  // polynomial weights: b as a function of x = 2 r^2 / a^2 - 1 in [-1, 1]
+  {
+    auto bx = [&](double x) {
+      double t = std::min(1.0, std::max(0.0, 0.5 * (x + 1.0)));  // (r/a)^2
+      return std::cyl_bessel_i(0.0, alpha * std::sqrt(1.0 - t)) / i0a;
+    };
+    double mono[POLY_N];
+    chebyshev_power_basis(bx, mono);
+    for (int k = 0; k < POLY_N; ++k) c->poly[k] = (float)mono[k];
+    // measured error of the FP32 Horner evaluation the device performs
+    double worst = 0;
+    for (int i = 0; i <= 20000; ++i) {
+      const float x = -1.0f + 2.0f * (float)i / 20000.0f;
+      float p = c->poly[POLY_N - 1];
+      for (int k = POLY_N - 2; k >= 0; --k) p = std::fma(p, x, c->poly[k]);
+      worst = std::max(worst, std::fabs((double)p - bx((double)x)));
+    }
+    c->poly_err = worst;
+  }
 
   c->tuner.init(c);
   *out = c;
@@ -459,7 +509,7 @@ int fr_debug_fold(const float *r, const int *k, int m, int *out, void *stream) {
 }
 
 int fr_debug_blob(const fr_ctx *c, const float *r2, int m, int mode, float *out, void *stream) {
-  if (!c || m < 0 || (m > 0 && (!r2 || !out)) || (mode != 0 && mode != 1))
+  if (!c || m < 0 || (m > 0 && (!r2 || !out)) || mode < 0 || mode > 2)
     return FR_ERR_INVALID_ARG;
   InsertArgs a = base_args(c);
   cudaError_t e = launch_debug_blob(a, r2, m, mode, out, (cudaStream_t)stream);

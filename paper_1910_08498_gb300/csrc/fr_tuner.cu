@@ -29,10 +29,10 @@ const std::vector<Config> &config_space() {
   static const std::vector<Config> v = [] {
     std::vector<Config> c;
     for (int shape = 0; shape < num_gather_shapes(); ++shape)
-      for (int w : {W_LUT, W_LUT_L1, W_OTF})
-        for (int ch : {64, 128, 256}) c.push_back(Config{ALGO_GATHER, shape, w, ch, 0, 0});
+      for (int w : {W_LUT, W_POLY, W_OTF})
+        for (int ch : {32, 64, 128}) c.push_back(Config{ALGO_GATHER, shape, w, ch, 0, 0});
     for (int th : {128, 256})
-      for (int w : {W_LUT, W_OTF})
+      for (int w : {W_LUT, W_POLY})
         for (int sub : {256, 1024}) c.push_back(Config{ALGO_SCATTER, -1, w, 0, th, sub});
     return c;
   }();
@@ -44,10 +44,10 @@ std::string describe(const Config &c) {
   if (c.algo == ALGO_GATHER) {
     GatherShape s = gather_shape(c.shape);
     std::snprintf(b, sizeof b, "gather bx=%d by=%d zc=%d chunk=%d w=%s", s.bx, s.by, s.zc, c.chunk,
-                  c.wmode == W_LUT ? "lut" : c.wmode == W_LUT_L1 ? "lut-l1" : "otf");
+                  c.wmode == W_LUT ? "lut" : c.wmode == W_POLY ? "poly" : "otf");
   } else {
     std::snprintf(b, sizeof b, "scatter threads=%d sub=%d w=%s", c.threads, c.sub,
-                  c.wmode == W_LUT ? "lut" : "otf");
+                  c.wmode == W_LUT ? "lut" : c.wmode == W_POLY ? "poly" : "otf");
   }
   return b;
 }
@@ -68,7 +68,7 @@ void config_features(const Config &c, int S, int n, float a, float *f) {
   if (c.algo == ALGO_GATHER) {
     if (c.shape >= 0 && c.shape < 4) f[1 + c.shape] = 1.f;
     GatherShape s = gather_shape(c.shape);
-    f[6] = std::log2((float)c.chunk / 64.f) / 2.f;
+    f[6] = std::log2((float)c.chunk / 32.f) / 2.f;
     f[13] = s.zc / 8.f;
     f[14] = (float)(s.bx * s.by * s.zc) / 2048.f;
     f[15] = (float)(s.bx * s.by) / 256.f;
@@ -77,18 +77,18 @@ void config_features(const Config &c, int S, int n, float a, float *f) {
     f[8] = c.sub / 1024.f;
   }
   f[5] = c.wmode == W_OTF ? 1.f : 0.f;
-  f[12] = c.wmode == W_LUT_L1 ? 1.f : 0.f;
+  f[12] = c.wmode == W_POLY ? 1.f : 0.f;
   f[9] = S / 256.f;
   f[10] = std::log2((float)std::max(n, 1)) / 13.f;
   f[11] = a / 2.5f;
 }
 
 int default_config(const fr_ctx *c) {
-  // gather, 16 x 16 x 8 CTA, table weights through L1, 128-image warp lists
+  // gather, 16 x 16 x 8 CTA, polynomial weights, 64-image warp lists
   const auto &sp = config_space();
   for (int i = 0; i < (int)sp.size(); ++i)
-    if (sp[i].algo == ALGO_GATHER && sp[i].shape == 0 && sp[i].wmode == W_LUT_L1 &&
-        sp[i].chunk == 128 && config_valid(c, i))
+    if (sp[i].algo == ALGO_GATHER && sp[i].shape == 0 && sp[i].wmode == W_POLY &&
+        sp[i].chunk == 64 && config_valid(c, i))
       return i;
   for (int i = 0; i < (int)sp.size(); ++i)
     if (config_valid(c, i)) return i;

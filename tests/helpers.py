@@ -36,6 +36,9 @@ def gpu_insert(S, batches, a=A32, alpha=ALPHA, config=-1, tuning=True, table=100
     on the GPU; returns (V complex128 flat, W float64 flat, report)."""
     ctx = L.fr_create(S, a, alpha, 0, table)
     try:
+        if config >= 0 and not L.fr_config_valid(ctx, config):
+            import pytest
+            pytest.skip(f"configuration {config} cannot run for this context")
         L.fr_set_options(ctx, forced_config=config, tuning=int(tuning), steps_per_insert=steps,
                          search=search, budget=budget)
         for img, rot in batches:

@@ -72,8 +72,8 @@ def test_configuration_space(lib):
     descs = [L.fr_describe_config(i) for i in range(n)]
     assert len(set(descs)) == n
     assert sum(d.startswith("gather") for d in descs) == 36
-    assert sum("w=otf" in d for d in descs) == 16
-    assert sum("w=lut-l1" in d for d in descs) == 12
+    assert sum("w=otf" in d for d in descs) == 12
+    assert sum("w=poly" in d for d in descs) == 16
     with pytest.raises(L.FrError):
         L.fr_describe_config(n)
 

@@ -63,7 +63,7 @@ def test_blob_table_and_on_the_fly(a, alpha, table):
         r2 = np.linspace(0, a2, 20001, dtype=np.float32)
         r2_d = torch.from_numpy(r2).cuda()
         ref = np.array([oracle.blob_r2(float(x), a, alpha) for x in r2[::10]])
-        for mode, tol in [(0, 3e-7 if table >= 10000 else 2e-6), (1, 1e-6)]:
+        for mode, tol in [(0, 3e-7 if table >= 10000 else 2e-6), (1, 1e-6), (2, 1e-6)]:
             out = torch.empty_like(r2_d)
             L.fr_debug_blob(ctx, r2_d, mode, out)
             got = out.cpu().numpy()[::10].astype(np.float64)
