@@ -77,31 +77,35 @@ __device__ __forceinline__ float2 ld_px(const unsigned char *p) {
   return __ldg(reinterpret_cast<const float2 *>(p));
 }
 
-// Fast path: every pixel of the box is stored (SGN = +1: pixels (kx0+j,
-// ky0+l)) or point-reflected (SGN = -1: pixels (-kx0-j, -ky0-l), conjugated
-// by the caller); no fold, range or multiplicity test.
-template <int WMODE, int KB, int F16, int SGN>
+// Fast path: every pixel of the box is stored (sgn = +1: pixels (kx0+j,
+// ky0+l)) or point-reflected (sgn = -1: pixels (-kx0-j, -ky0-l), conjugated
+// by the caller); no fold, range or multiplicity test.  One copy of the body
+// serves both (runtime sign), rows are not unrolled, and a row whose distance
+// to the voxel already exceeds a is skipped.
+template <int WMODE, int KB, int F16>
 __device__ __forceinline__ void box_fast(const InsertArgs &args, const float2 *lut,
-                                         const unsigned char *ibase, int kx0, int ky0, float fx,
-                                         float fy, float uz2, float inv_a2, float &sr, float &si,
-                                         float &sw) {
+                                         const unsigned char *ibase, int sgn, int kx0, int ky0,
+                                         float fx, float fy, float uz2, float inv_a2, float &sr,
+                                         float &si, float &sw) {
   const Geom &g = args.g;
   constexpr int ESZ = F16 ? 4 : 8;
-  const size_t row_bytes = (size_t)g.NX * ESZ;
-#pragma unroll
+  const int row_bytes = g.NX * ESZ;
+  const int step = sgn * ESZ;
+#pragma unroll 1
   for (int l = 0; l < KB; ++l) {
-    int ky = SGN * (ky0 + l);
-    ky += ky < 0 ? g.S : 0;
-    const unsigned char *row = ibase + (size_t)ky * row_bytes + (size_t)(SGN * kx0) * ESZ;
     const float dy = fy - (float)l;
     const float ry = fmaf(dy, dy, uz2);
+    if (ry > g.a2) continue;
+    int ky = sgn * (ky0 + l);
+    ky += ky < 0 ? g.S : 0;
+    const unsigned char *row = ibase + (ky * row_bytes + sgn * kx0 * ESZ);
 #pragma unroll
     for (int j = 0; j < KB; ++j) {
       const float dx = fx - (float)j;
       const float r2 = fmaf(dx, dx, ry);
       if (r2 <= g.a2) {
         const float w = blob_w<WMODE>(lut, r2, args, inv_a2);
-        const float2 p = ld_px<F16>(row + SGN * j * ESZ);
+        const float2 p = ld_px<F16>(row + j * step);
         sr = fmaf(w, p.x, sr);
         si = fmaf(w, p.y, si);
         sw += w;
@@ -194,6 +198,12 @@ gather_kernel(const InsertArgs args) {
   const float rw = sqrtf(3.5f * 3.5f + 1.5f * 1.5f + hz * hz);
   const float a = g.a;
   const float inv_a2 = 1.0f / g.a2;
+  // The box starts at ceil(u - a_box).  When the box has a spare cell
+  // (KB > floor(2a) + 1) it is shifted down by a small margin, so a pixel at
+  // distance exactly a (possible for the DC pixel, which sits at q = 0) is
+  // never lost to rounding of u; the r^2 <= a^2 test decides it.
+  const float a_box = KB > (int)floorf(2.0f * a) + 1 ? a + 1e-4f : a;
+  const float a_plane = a + 1e-4f;  // conservative |u_z| <= a test for queueing
   const float cull = a + rw + 1e-3f;
   const float reach = (float)g.H + a;     // the extended plane spans [-H, H]^2
   const float ext = reach + rw + 1.0f;
@@ -250,19 +260,21 @@ gather_kernel(const InsertArgs args) {
       const float uz = fmaf(LF(LF_MZ, li), sdz, fmaf(LF(LF_MY, li), sdy, fmaf(LF(LF_MX, li), sdx, LF(LF_UZ, li))));
       const float uxr = fmaf(LF(LF_E1Z, li), sdz, fmaf(LF(LF_E1Y, li), sdy, fmaf(LF(LF_E1X, li), sdx, LF(LF_FX, li))));
       const float uyr = fmaf(LF(LF_E2Z, li), sdz, fmaf(LF(LF_E2Y, li), sdy, fmaf(LF(LF_E2X, li), sdx, LF(LF_FY, li))));
-      const float ixf = ceilf(uxr - a), iyf = ceilf(uyr - a);
+      const float ixf = ceilf(uxr - a_box), iyf = ceilf(uyr - a_box);
       const float fx = uxr - ixf, fy = uyr - iyf;
       const int kx0 = LI(LF_CIX, li) + (int)ixf, ky0 = LI(LF_CIY, li) + (int)iyf;
       const float uz2 = uz * uz;
       const unsigned char *ibase = imgs + (size_t)LI(LF_IMG, li) * img_stride;
       const bool fold_vox = sx <= -g.xa0;
       float sr = 0.f, si = 0.f, sw = 0.f;
-      if (!fold_vox && kx0 >= 1 && kx0 + KB - 1 <= g.H && ky0 >= -g.H && ky0 + KB - 1 < g.H) {
-        box_fast<WMODE, KB, F16, 1>(args, lut, ibase, kx0, ky0, fx, fy, uz2, inv_a2, sr, si, sw);
-      } else if (!fold_vox && kx0 + KB - 1 <= -1 && kx0 >= -g.H && ky0 > -g.H &&
-                 ky0 + KB - 1 <= g.H) {
-        box_fast<WMODE, KB, F16, -1>(args, lut, ibase, kx0, ky0, fx, fy, uz2, inv_a2, sr, si, sw);
-        si = -si;
+      const bool direct =
+          !fold_vox && kx0 >= 1 && kx0 + KB - 1 <= g.H && ky0 >= -g.H && ky0 + KB - 1 < g.H;
+      const bool mirror = !fold_vox && kx0 + KB - 1 <= -1 && kx0 >= -g.H && ky0 > -g.H &&
+                          ky0 + KB - 1 <= g.H;
+      if (direct || mirror) {
+        const int sgn = direct ? 1 : -1;
+        box_fast<WMODE, KB, F16>(args, lut, ibase, sgn, kx0, ky0, fx, fy, uz2, inv_a2, sr, si, sw);
+        si *= (float)sgn;
       } else {
         const float vr2 = (float)(sx * sx + sy * sy + sz * sz);
         box_careful<WMODE, KB, F16>(args, lut, ibase, LF(LF_E1X, li), LF(LF_E2X, li), kx0, ky0,
@@ -292,7 +304,7 @@ gather_kernel(const InsertArgs args) {
       const float dz = (float)(z0 + t) - cz;
       const float uz = fmaf(mz, dz, bz);
       const float ux = cix + fmaf(e1z, dz, bx), uy = ciy + fmaf(e2z, dz, by);
-      const bool hit = fabsf(uz) <= a && fabsf(ux) <= reach && fabsf(uy) <= reach;
+      const bool hit = fabsf(uz) <= a_plane && fabsf(ux) <= reach && fabsf(uy) <= reach;
       mask |= (hit ? 1u : 0u) << t;
     }
     if (!col_in) mask = 0;

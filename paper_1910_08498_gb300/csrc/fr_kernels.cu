@@ -35,18 +35,17 @@ __global__ void scatter_kernel(const InsertArgs args) {
     __syncthreads();
   }
   const float a = g.a, a2 = g.a2, inv_a2 = 1.0f / a2;
-  const size_t total = (size_t)args.n * g.S * g.NX;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int kx = (int)(idx % g.NX);
-    const size_t r = idx / g.NX;
-    const int row = (int)(r % g.S);
-    const int i = (int)(r / g.S);
+  const int npx = g.S * g.NX;           // stored pixels per image
+  const int i = blockIdx.y;             // image of this CTA row
+  const float *R = args.rot + 9 * (size_t)i;
+  const float R00 = __ldg(R + 0), R01 = __ldg(R + 1), R10 = __ldg(R + 3), R11 = __ldg(R + 4),
+              R20 = __ldg(R + 6), R21 = __ldg(R + 7);
+  const size_t ibase = (size_t)i * npx;
+  for (int px = blockIdx.x * blockDim.x + threadIdx.x; px < npx; px += gridDim.x * blockDim.x) {
+    const int row = px / g.NX;
+    const int kx = px - row * g.NX;
     const int ky = row < g.H ? row : row - g.S;
-    const float *R = args.rot + 9 * (size_t)i;
-    const float R00 = __ldg(R + 0), R01 = __ldg(R + 1), R10 = __ldg(R + 3), R11 = __ldg(R + 4),
-                R20 = __ldg(R + 6), R21 = __ldg(R + 7);
-    float2 p = load_pixel(args.images, args.f16, idx);
+    float2 p = load_pixel(args.images, args.f16, ibase + px);
     float qxh, qxl, qyh, qyl, qzh, qzl;
     rk_dd(R00, R01, (float)kx, (float)ky, qxh, qxl);
     rk_dd(R10, R11, (float)kx, (float)ky, qyh, qyl);
@@ -60,17 +59,16 @@ __global__ void scatter_kernel(const InsertArgs args) {
 #pragma unroll 1
     for (int dz = 0; dz < KB; ++dz) {
       const int z = z0 + dz;
-      if (z < -g.H || z > g.H) continue;
       const float fz = ((float)z - qzh) - qzl;
       const float rz = fz * fz;
-      if (rz > a2) continue;
-#pragma unroll
+      if (z < -g.H || z > g.H || rz > a2) continue;
+#pragma unroll 1
       for (int dy = 0; dy < KB; ++dy) {
         const int y = y0 + dy;
         const float fy = ((float)y - qyh) - qyl;
         const float ryz = fmaf(fy, fy, rz);
         if (y < -g.H || y > g.H || ryz > a2) continue;
-        const size_t rowbase = ((size_t)(z + g.H) * g.D + (size_t)(y + g.H)) * g.NXa;
+        float4 *rowp = args.scratch + ((size_t)(z + g.H) * g.D + (size_t)(y + g.H)) * g.NXa - g.xa0;
 #pragma unroll
         for (int dx = 0; dx < KB; ++dx) {
           const int x = x0 + dx;
@@ -78,8 +76,7 @@ __global__ void scatter_kernel(const InsertArgs args) {
           const float r2 = fmaf(fx, fx, ryz);
           if (r2 <= a2 && x <= g.H && x >= g.xa0) {
             const float w = blob_w<WMODE>(s_lut, r2, args, inv_a2);
-            atomicAdd(args.scratch + rowbase + (size_t)(x - g.xa0),
-                      make_float4(w * p.x, w * p.y, w, 0.f));
+            atomicAdd(rowp + x, make_float4(w * p.x, w * p.y, w, 0.f));
           }
         }
       }
@@ -243,9 +240,11 @@ static cudaError_t launch_scatter_t(int threads, const InsertArgs &a, cudaStream
     attr_set = true;
   }
   if (query_only) return cudaSuccess;
-  size_t work = (size_t)a.n * a.g.S * a.g.NX;
-  int blocks = grid_for(work, threads, sm_count() * (2048 / threads));
-  fn<<<blocks, threads, smem, st>>>(a);
+  if (a.n <= 0) return cudaSuccess;
+  if (a.n > 65535) return cudaErrorInvalidValue;
+  const int npx = a.g.S * a.g.NX;
+  dim3 grid((npx + threads - 1) / threads, a.n);
+  fn<<<grid, threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
