@@ -36,7 +36,14 @@
 //  4. write back (A5): every FLUSH list images and at the end, the warp folds
 //     its shared-memory partial sums into the HBM double-float accumulators
 //     (error-free TwoSum), so no FP32 partial sum runs over more than FLUSH
-//     images.
+//     images.  A launch may split the images of a batch across nsplit CTAs
+//     per brick (the bricks at the centre meet every plane and would otherwise
+//     run alone at the end); then each CTA adds its partial sums to a float4
+//     scratch volume with atomics, folded into the accumulators after the
+//     launch.
+//  Fast and careful items are queued apart, so a careful item never holds a
+//  whole round of fast ones; for polynomial weights the fast box is branch
+//  free (packed FP32x2 FMAs, weights masked to 0 outside the blob).
 #pragma once
 
 #include "fr_device.cuh"
@@ -69,7 +76,6 @@ __device__ __forceinline__ bool col_in_any(const Geom &g, int fx0, int fy0) {
 }
 
 constexpr int GATHER_FLUSH = 256;  // list images between flushes of the shared partial sums
-constexpr int GATHER_QUEUE_SLACK = 64;  // queue entries per warp beyond one image's worth
 
 template <int F16>
 __device__ __forceinline__ float2 ld_px(const unsigned char *p) {
@@ -112,6 +118,50 @@ __device__ __forceinline__ void box_fast(const InsertArgs &args, const float2 *l
       }
     }
   }
+}
+
+// Branch-free fast box for the polynomial weights: every candidate of the
+// KB x KB box is evaluated (the pixels of a fast box all exist), the weight is
+// masked to 0 outside r <= a, so all lanes stay converged.  The polynomial is
+// split into even and odd parts, E(x^2) + x O(x^2), evaluated together with
+// packed FP32x2 FMAs (c holds (c_0, c_1), (c_2, c_3), ... pairs).
+template <int KB, int F16>
+__device__ __forceinline__ void box_fast_poly(const InsertArgs &args, const float2 *c,
+                                              const unsigned char *ibase, int sgn, int kx0,
+                                              int ky0, float fx, float fy, float uz2,
+                                              float two_inv_a2, float &sr, float &si,
+                                              float &sw) {
+  const Geom &g = args.g;
+  constexpr int ESZ = F16 ? 4 : 8;
+  constexpr int NP = POLY_N / 2;
+  const int row_bytes = g.NX * ESZ;
+  const int step = sgn * ESZ;
+  float2 acc = make_float2(sr, si);
+#pragma unroll 1
+  for (int l = 0; l < KB; ++l) {
+    const float dy = fy - (float)l;
+    const float ry = fmaf(dy, dy, uz2);
+    if (ry > g.a2) continue;
+    int ky = sgn * (ky0 + l);
+    ky += ky < 0 ? g.S : 0;
+    const unsigned char *row = ibase + (ky * row_bytes + sgn * kx0 * ESZ);
+#pragma unroll
+    for (int j = 0; j < KB; ++j) {
+      const float dx = fx - (float)j;
+      const float r2 = fmaf(dx, dx, ry);
+      const float x = fmaf(r2, two_inv_a2, -1.0f);
+      const float x2 = x * x;
+      float2 eo = c[NP - 1];
+#pragma unroll
+      for (int k = NP - 2; k >= 0; --k) eo = __ffma2_rn(eo, make_float2(x2, x2), c[k]);
+      const float w = r2 <= g.a2 ? fmaf(eo.y, x, eo.x) : 0.0f;
+      const float2 p = ld_px<F16>(row + j * step);
+      acc = __ffma2_rn(make_float2(w, w), p, acc);
+      sw += w;
+    }
+  }
+  sr = acc.x;
+  si = acc.y;
 }
 
 // Careful path: any box, exact fold predicate (when near the fold plane) and
@@ -161,11 +211,11 @@ __device__ __noinline__ void box_careful(const InsertArgs &args, const float2 *l
 }
 
 template <int BX, int BY, int ZC, int WMODE, int KB, int F16>
-__global__ void __launch_bounds__(BX * BY)
+__global__ void __launch_bounds__(BX * BY, 2)
 gather_kernel(const InsertArgs args) {
   constexpr int NT = BX * BY;
-  constexpr int NW = NT / 32;
-  constexpr int WV = 32 * ZC;  // voxels per warp footprint
+  constexpr int WV = 32 * ZC;                   // voxels per warp footprint
+  constexpr int QCAP = WV + 32;                 // entries per queue
   constexpr int ESZ = F16 ? 4 : 8;
   static_assert(BX % 8 == 0 && BY % 4 == 0 && NT % 32 == 0, "warp footprint is 8 x 4 columns");
   static_assert(ZC <= 8, "item encoding holds 3 bits of z");
@@ -178,21 +228,25 @@ gather_kernel(const InsertArgs args) {
   unsigned char *sp = smem;
   float2 *s_lut = reinterpret_cast<float2 *>(sp);
   if (WMODE == W_LUT) sp += ((size_t)args.lut_n * sizeof(float2) + 15) & ~(size_t)15;
-  const size_t per_warp =
-      (size_t)LIST_FIELDS * lcap * 4 + (size_t)3 * WV * 4 + (size_t)(WV + GATHER_QUEUE_SLACK) * 4;
+  const size_t per_warp = (size_t)LIST_FIELDS * lcap * 4 + (size_t)3 * WV * 4 + (size_t)2 * QCAP * 4;
   sp += (size_t)warp * per_warp;
-  float *s_list = reinterpret_cast<float *>(sp);  // [LIST_FIELDS][lcap]
+  float *s_list = reinterpret_cast<float *>(sp);         // [LIST_FIELDS][lcap]
   float *s_acc = s_list + (size_t)LIST_FIELDS * lcap;   // [3][WV]
-  unsigned *s_q = reinterpret_cast<unsigned *>(s_acc + 3 * WV);
+  unsigned *s_qf = reinterpret_cast<unsigned *>(s_acc + 3 * WV);  // fast items
+  unsigned *s_qc = s_qf + QCAP;                                    // careful items
   const float2 *lut = s_lut;
   auto LF = [&](int f, int i) -> float & { return s_list[f * lcap + i]; };
   auto LI = [&](int f, int i) -> int { return __float_as_int(s_list[f * lcap + i]); };
 
-  // this warp's footprint: 8 x 4 columns, ZC deep
+  // this CTA's brick and image range, this warp's footprint (8 x 4 columns, ZC deep)
+  const int nbz = args.nbz;
+  const int bz = blockIdx.z % nbz, split = blockIdx.z / nbz;
+  const int img0 = (int)((long long)args.n * split / args.nsplit);
+  const int img1 = (int)((long long)args.n * (split + 1) / args.nsplit);
   const int wx = warp % (BX / 8), wy = warp / (BX / 8);
   const int fx0 = g.xa0 + blockIdx.x * BX + wx * 8;
   const int fy0 = -g.H + blockIdx.y * BY + wy * 4;
-  const int z0 = -g.H + blockIdx.z * ZC;
+  const int z0 = -g.H + bz * ZC;
   const float cx = fx0 + 3.5f, cy = fy0 + 1.5f, cz = z0 + 0.5f * (ZC - 1);  // footprint centre
   const float hz = 0.5f * (ZC - 1);
   const float rw = sqrtf(3.5f * 3.5f + 1.5f * 1.5f + hz * hz);
@@ -205,13 +259,17 @@ gather_kernel(const InsertArgs args) {
   const float a_box = KB > (int)floorf(2.0f * a) + 1 ? a + 1e-4f : a;
   const float a_plane = a + 1e-4f;  // conservative |u_z| <= a test for queueing
   const float cull = a + rw + 1e-3f;
-  const float reach = (float)g.H + a;     // the extended plane spans [-H, H]^2
+  const float reach = (float)g.H + a;  // the extended plane spans [-H, H]^2
   const float ext = reach + rw + 1.0f;
   const int vx = fx0 + (lane & 7), vy = fy0 + (lane >> 3);
   const float dvx = (float)vx - cx, dvy = (float)vy - cy;
   const bool col_in = vx <= g.H && vy <= g.H;
+  const bool fold_col = vx <= -g.xa0;  // x <= floor(a): pixels from both sides of the fold
   const unsigned char *imgs = reinterpret_cast<const unsigned char *>(args.images);
   const size_t img_stride = (size_t)g.S * g.NX * ESZ;
+  float2 cpair[POLY_N / 2];
+#pragma unroll
+  for (int k = 0; k < POLY_N / 2; ++k) cpair[k] = make_float2(args.poly[2 * k], args.poly[2 * k + 1]);
 
   if (WMODE == W_LUT) {
     for (int i = tid; i < args.lut_n; i += NT) s_lut[i] = args.lut[i];
@@ -220,7 +278,9 @@ gather_kernel(const InsertArgs args) {
   for (int i = lane; i < 3 * WV; i += 32) s_acc[i] = 0.f;
   __syncwarp();
 
-  // fold the warp's shared partial sums into HBM (lane owns its column's voxels)
+  // fold the warp's shared partial sums into HBM (lane owns its column's voxels):
+  // straight into the double-float accumulators when this CTA is the only one
+  // writing its brick, else into the float4 scratch (merged after the launch)
   auto flush = [&]() {
     __syncwarp();
     if (col_in) {
@@ -230,14 +290,20 @@ gather_kernel(const InsertArgs args) {
         if (vz > g.H) break;
         const size_t v =
             ((size_t)(vz + g.H) * g.D + (size_t)(vy + g.H)) * g.NXa + (size_t)(vx - g.xa0);
+        const float ar = s_acc[lane * ZC + t], ai = s_acc[WV + lane * ZC + t],
+                    aw = s_acc[2 * WV + lane * ZC + t];
+        if (aw != 0.f || ar != 0.f || ai != 0.f) {
+          if (args.nsplit == 1) {
+            const float add[3] = {ar, ai, aw};
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float add = s_acc[c * WV + lane * ZC + t];
-          if (add != 0.f) {
-            float h = args.acc[c * args.plane + v], l = args.acc[(3 + c) * args.plane + v];
-            dd_add(h, l, add);
-            args.acc[c * args.plane + v] = h;
-            args.acc[(3 + c) * args.plane + v] = l;
+            for (int c = 0; c < 3; ++c) {
+              float h = args.acc[c * args.plane + v], l = args.acc[(3 + c) * args.plane + v];
+              dd_add(h, l, add[c]);
+              args.acc[c * args.plane + v] = h;
+              args.acc[(3 + c) * args.plane + v] = l;
+            }
+          } else {
+            atomicAdd(args.scratch + v, make_float4(ar, ai, aw, 0.f));
           }
         }
       }
@@ -249,66 +315,89 @@ gather_kernel(const InsertArgs args) {
     __syncwarp();
   };
 
-  // process every queued (image, voxel) item; one item per lane per round
-  auto drain = [&](int qlen) {
-    __syncwarp();
-    for (int k = lane; k < qlen; k += 32) {
-      const unsigned it = s_q[k];
-      const int li = (int)(it >> 8), src = (int)((it >> 3) & 31), t = (int)(it & 7);
-      const int sx = fx0 + (src & 7), sy = fy0 + (src >> 3), sz = z0 + t;
-      const float sdx = (float)sx - cx, sdy = (float)sy - cy, sdz = (float)sz - cz;
-      const float uz = fmaf(LF(LF_MZ, li), sdz, fmaf(LF(LF_MY, li), sdy, fmaf(LF(LF_MX, li), sdx, LF(LF_UZ, li))));
-      const float uxr = fmaf(LF(LF_E1Z, li), sdz, fmaf(LF(LF_E1Y, li), sdy, fmaf(LF(LF_E1X, li), sdx, LF(LF_FX, li))));
-      const float uyr = fmaf(LF(LF_E2Z, li), sdz, fmaf(LF(LF_E2Y, li), sdy, fmaf(LF(LF_E2X, li), sdx, LF(LF_FY, li))));
-      const float ixf = ceilf(uxr - a_box), iyf = ceilf(uyr - a_box);
-      const float fx = uxr - ixf, fy = uyr - iyf;
-      const int kx0 = LI(LF_CIX, li) + (int)ixf, ky0 = LI(LF_CIY, li) + (int)iyf;
-      const float uz2 = uz * uz;
-      const unsigned char *ibase = imgs + (size_t)LI(LF_IMG, li) * img_stride;
-      const bool fold_vox = sx <= -g.xa0;
-      float sr = 0.f, si = 0.f, sw = 0.f;
-      const bool direct =
-          !fold_vox && kx0 >= 1 && kx0 + KB - 1 <= g.H && ky0 >= -g.H && ky0 + KB - 1 < g.H;
-      const bool mirror = !fold_vox && kx0 + KB - 1 <= -1 && kx0 >= -g.H && ky0 > -g.H &&
-                          ky0 + KB - 1 <= g.H;
-      if (direct || mirror) {
-        const int sgn = direct ? 1 : -1;
+  // one queued (image, voxel) item: form the box sums and add them to the
+  // warp's partial sums
+  auto process = [&](unsigned it, bool careful) {
+    const int li = (int)(it >> 9), src = (int)((it >> 3) & 31), t = (int)(it & 7);
+    const int sgn = (it >> 8) & 1 ? -1 : 1;
+    const int sx = fx0 + (src & 7), sy = fy0 + (src >> 3), sz = z0 + t;
+    const float sdx = (float)sx - cx, sdy = (float)sy - cy, sdz = (float)sz - cz;
+    const float uz = fmaf(LF(LF_MZ, li), sdz, fmaf(LF(LF_MY, li), sdy, fmaf(LF(LF_MX, li), sdx, LF(LF_UZ, li))));
+    const float uxr = fmaf(LF(LF_E1Z, li), sdz, fmaf(LF(LF_E1Y, li), sdy, fmaf(LF(LF_E1X, li), sdx, LF(LF_FX, li))));
+    const float uyr = fmaf(LF(LF_E2Z, li), sdz, fmaf(LF(LF_E2Y, li), sdy, fmaf(LF(LF_E2X, li), sdx, LF(LF_FY, li))));
+    const float ixf = ceilf(uxr - a_box), iyf = ceilf(uyr - a_box);
+    const float fx = uxr - ixf, fy = uyr - iyf;
+    const int kx0 = LI(LF_CIX, li) + (int)ixf, ky0 = LI(LF_CIY, li) + (int)iyf;
+    const float uz2 = uz * uz;
+    const unsigned char *ibase = imgs + (size_t)LI(LF_IMG, li) * img_stride;
+    float sr = 0.f, si = 0.f, sw = 0.f;
+    if (!careful) {
+      if (WMODE == W_POLY)
+        box_fast_poly<KB, F16>(args, cpair, ibase, sgn, kx0, ky0, fx, fy, uz2, 2.0f * inv_a2, sr,
+                               si, sw);
+      else
         box_fast<WMODE, KB, F16>(args, lut, ibase, sgn, kx0, ky0, fx, fy, uz2, inv_a2, sr, si, sw);
-        si *= (float)sgn;
-      } else {
-        const float vr2 = (float)(sx * sx + sy * sy + sz * sz);
-        box_careful<WMODE, KB, F16>(args, lut, ibase, LF(LF_E1X, li), LF(LF_E2X, li), kx0, ky0,
-                                    fx, fy, uz2, fold_vox, vr2, inv_a2, sr, si, sw);
-      }
-      const int slot = src * ZC + t;
-      atomicAdd(&s_acc[slot], sr);
-      atomicAdd(&s_acc[WV + slot], si);
-      atomicAdd(&s_acc[2 * WV + slot], sw);
+      si *= (float)sgn;
+    } else {
+      const float vr2 = (float)(sx * sx + sy * sy + sz * sz);
+      box_careful<WMODE, KB, F16>(args, lut, ibase, LF(LF_E1X, li), LF(LF_E2X, li), kx0, ky0, fx,
+                                  fy, uz2, sx <= -g.xa0, vr2, inv_a2, sr, si, sw);
     }
+    const int slot = src * ZC + t;
+    atomicAdd(&s_acc[slot], sr);
+    atomicAdd(&s_acc[WV + slot], si);
+    atomicAdd(&s_acc[2 * WV + slot], sw);
+  };
+
+  // drain full rounds of 32 items (all of them if `all`); the remainder moves
+  // to the front of the queue
+  auto drain = [&](unsigned *q, int &qlen, bool careful, bool all) {
+    __syncwarp();
+    const int nfull = all ? qlen : (qlen & ~31);
+    for (int k = lane; k < nfull; k += 32) process(q[k], careful);
+    __syncwarp();
+    const int rest = qlen - nfull;
+    if (rest) {
+      unsigned v = lane < rest ? q[nfull + lane] : 0u;
+      __syncwarp();
+      if (lane < rest) q[lane] = v;
+    }
+    qlen = rest;
     __syncwarp();
   };
 
-  // queue the footprint's voxels near the plane of list entry li and inside
-  // the image's reach; drain when the queue could overflow
-  int qlen = 0;
+  // queue the footprint's voxels near the plane of list entry li that the
+  // extended plane reaches, fast and careful ones apart
+  int qf = 0, qc = 0;
   auto enqueue = [&](int li) {
     const float mx = LF(LF_MX, li), my = LF(LF_MY, li), mz = LF(LF_MZ, li);
     const float bz = fmaf(my, dvy, fmaf(mx, dvx, LF(LF_UZ, li)));
     const float bx = fmaf(LF(LF_E1Y, li), dvy, fmaf(LF(LF_E1X, li), dvx, LF(LF_FX, li)));
     const float by = fmaf(LF(LF_E2Y, li), dvy, fmaf(LF(LF_E2X, li), dvx, LF(LF_FY, li)));
-    const float cix = (float)LI(LF_CIX, li), ciy = (float)LI(LF_CIY, li);
+    const int cix = LI(LF_CIX, li), ciy = LI(LF_CIY, li);
     const float e1z = LF(LF_E1Z, li), e2z = LF(LF_E2Z, li);
-    unsigned mask = 0;
+    unsigned mf = 0, mc = 0, mneg = 0;
 #pragma unroll
     for (int t = 0; t < ZC; ++t) {
       const float dz = (float)(z0 + t) - cz;
       const float uz = fmaf(mz, dz, bz);
-      const float ux = cix + fmaf(e1z, dz, bx), uy = ciy + fmaf(e2z, dz, by);
-      const bool hit = fabsf(uz) <= a_plane && fabsf(ux) <= reach && fabsf(uy) <= reach;
-      mask |= (hit ? 1u : 0u) << t;
+      const float uxr = fmaf(e1z, dz, bx), uyr = fmaf(e2z, dz, by);
+      const float ux = (float)cix + uxr, uy = (float)ciy + uyr;
+      if (fabsf(uz) <= a_plane && fabsf(ux) <= reach && fabsf(uy) <= reach) {
+        const int kx0 = cix + (int)ceilf(uxr - a_box), ky0 = ciy + (int)ceilf(uyr - a_box);
+        const bool direct = kx0 >= 1 && kx0 + KB - 1 <= g.H && ky0 >= -g.H && ky0 + KB - 1 < g.H;
+        const bool mirror = kx0 + KB - 1 <= -1 && kx0 >= -g.H && ky0 > -g.H && ky0 + KB - 1 <= g.H;
+        if (!fold_col && (direct || mirror)) {
+          mf |= 1u << t;
+          if (mirror) mneg |= 1u << t;
+        } else {
+          mc |= 1u << t;
+        }
+      }
     }
-    if (!col_in) mask = 0;
-    const int cnt = __popc(mask);
+    if (!col_in) mf = mc = 0;
+    // warp prefix sums of both counts (packed 16 + 16 bits)
+    const int cnt = __popc(mf) | (__popc(mc) << 16);
     int incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -316,17 +405,23 @@ gather_kernel(const InsertArgs args) {
       if (lane >= o) incl += v;
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
-    int pos = qlen + incl - cnt;
-    while (mask) {
-      const int t = __ffs(mask) - 1;
-      mask &= mask - 1;
-      s_q[pos++] = ((unsigned)li << 8) | ((unsigned)lane << 3) | (unsigned)t;
+    const int excl = incl - cnt;
+    int pf = qf + (excl & 0xffff), pc = qc + (excl >> 16);
+    const unsigned base = ((unsigned)li << 9) | ((unsigned)lane << 3);
+    while (mf) {
+      const int t = __ffs(mf) - 1;
+      mf &= mf - 1;
+      s_qf[pf++] = base | (((mneg >> t) & 1u) << 8) | (unsigned)t;
     }
-    qlen += total;
-    if (qlen > GATHER_QUEUE_SLACK) {
-      drain(qlen);
-      qlen = 0;
+    while (mc) {
+      const int t = __ffs(mc) - 1;
+      mc &= mc - 1;
+      s_qc[pc++] = base | (unsigned)t;
     }
+    qf += total & 0xffff;
+    qc += total >> 16;
+    if (qf >= 32) drain(s_qf, qf, false, false);
+    if (qc >= 32) drain(s_qc, qc, true, false);
   };
 
   const float *rot = args.rot;
@@ -336,21 +431,24 @@ gather_kernel(const InsertArgs args) {
     for (int li = 0; li < nl; ++li) {
       enqueue(li);
       if (++since_flush >= GATHER_FLUSH) {
-        if (qlen) { drain(qlen); qlen = 0; }
+        drain(s_qf, qf, false, true);
+        drain(s_qc, qc, true, true);
         flush();
         since_flush = 0;
       }
     }
-    if (qlen) { drain(qlen); qlen = 0; }
+    // the list is rebuilt next: nothing may refer to it afterwards
+    drain(s_qf, qf, false, true);
+    drain(s_qc, qc, true, true);
     nl = 0;
   };
 
   // ---- cull: one image per lane; kept images go to the warp's list in order
-  for (int cs = 0; cs < args.n; cs += 32) {
+  for (int cs = img0; cs < img1; cs += 32) {
     const int i = cs + lane;
     bool keep = false;
     float e1x = 0, e1y = 0, e1z = 0, e2x = 0, e2y = 0, e2z = 0, mx = 0, my = 0, mz = 0;
-    if (i < args.n) {
+    if (i < img1) {
       const float *R = rot + 9 * (size_t)i;
       e1x = __ldg(R + 0); e1y = __ldg(R + 3); e1z = __ldg(R + 6);
       e2x = __ldg(R + 1); e2y = __ldg(R + 4); e2z = __ldg(R + 7);

@@ -30,12 +30,11 @@ size_t gather_smem_bytes(const GatherShape &sh, int wmode, int lut_n, int chunk)
   size_t b = 0;
   if (wmode == W_LUT) b += up16((size_t)lut_n * sizeof(float2));
   // per warp: image list, partial sums, item queue
-  b += (size_t)nw * ((size_t)LIST_FIELDS * chunk * 4 + (size_t)3 * wv * 4 +
-                     (size_t)(wv + GATHER_QUEUE_SLACK) * 4);
+  b += (size_t)nw * ((size_t)LIST_FIELDS * chunk * 4 + (size_t)3 * wv * 4 + (size_t)2 * (wv + 32) * 4);
   return b;
 }
 
-int gather_queue_len() { return GATHER_QUEUE_SLACK; }
+
 
 cudaError_t launch_gather(int shape_id, int wmode, const InsertArgs &a, cudaStream_t st,
                           int query_only, KernelInfo *info) {

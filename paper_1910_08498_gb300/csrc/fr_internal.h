@@ -53,7 +53,8 @@ struct InsertArgs {
   int *err;             // device error word
   // gather geometry
   int nbx, nby, nbz;    // bricks per axis
-  int chunk;            // images culled per list chunk (images per CTA barrier)
+  int chunk;            // capacity of a warp's image list
+  int nsplit;           // CTAs per brick, each taking a contiguous share of the images
   // scatter
   float4 *scratch;      // [z][y][x - xa0] (re, im, w, 0)
 };
@@ -91,7 +92,6 @@ int num_gather_shapes();
 GatherShape gather_shape(int id);
 // dynamic shared memory a gather launch needs
 size_t gather_smem_bytes(const GatherShape &sh, int wmode, int lut_n, int chunk);
-int gather_queue_len();
 
 // MLP kernels
 cudaError_t mlp_forward(const float *params, const float *x, int m, float *y, cudaStream_t st);

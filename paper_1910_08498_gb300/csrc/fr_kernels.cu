@@ -36,16 +36,18 @@ __global__ void scatter_kernel(const InsertArgs args) {
   }
   const float a = g.a, a2 = g.a2, inv_a2 = 1.0f / a2;
   const int npx = g.S * g.NX;           // stored pixels per image
-  const int i = blockIdx.y;             // image of this CTA row
-  const float *R = args.rot + 9 * (size_t)i;
-  const float R00 = __ldg(R + 0), R01 = __ldg(R + 1), R10 = __ldg(R + 3), R11 = __ldg(R + 4),
-              R20 = __ldg(R + 6), R21 = __ldg(R + 7);
-  const size_t ibase = (size_t)i * npx;
-  for (int px = blockIdx.x * blockDim.x + threadIdx.x; px < npx; px += gridDim.x * blockDim.x) {
+  const int total = args.n * npx;       // < 2^31: sub-batches hold at most 1024 images
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += gridDim.x * blockDim.x) {
+    const int i = idx / npx;
+    const int px = idx - i * npx;
     const int row = px / g.NX;
     const int kx = px - row * g.NX;
     const int ky = row < g.H ? row : row - g.S;
-    float2 p = load_pixel(args.images, args.f16, ibase + px);
+    const float *R = args.rot + 9 * (size_t)i;
+    const float R00 = __ldg(R + 0), R01 = __ldg(R + 1), R10 = __ldg(R + 3), R11 = __ldg(R + 4),
+                R20 = __ldg(R + 6), R21 = __ldg(R + 7);
+    float2 p = load_pixel(args.images, args.f16, idx);
     float qxh, qxl, qyh, qyl, qzh, qzl;
     rk_dd(R00, R01, (float)kx, (float)ky, qxh, qxl);
     rk_dd(R10, R11, (float)kx, (float)ky, qyh, qyl);
@@ -241,10 +243,10 @@ static cudaError_t launch_scatter_t(int threads, const InsertArgs &a, cudaStream
   }
   if (query_only) return cudaSuccess;
   if (a.n <= 0) return cudaSuccess;
-  if (a.n > 65535) return cudaErrorInvalidValue;
-  const int npx = a.g.S * a.g.NX;
-  dim3 grid((npx + threads - 1) / threads, a.n);
-  fn<<<grid, threads, smem, st>>>(a);
+  const long long work = (long long)a.n * a.g.S * a.g.NX;
+  if (work >= (1LL << 31)) return cudaErrorInvalidValue;
+  int blocks = grid_for((size_t)work, threads, sm_count() * (2048 / threads));
+  fn<<<blocks, threads, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -121,8 +121,20 @@ int run_config(fr_ctx *c, int id, const void *images, int f16, const float *rot,
   a.n = n;
   if (cfg.algo == ALGO_GATHER) {
     gather_geometry(c, cfg, a);
+    // split the images of large batches across several CTAs per brick so the
+    // bricks at the centre, which every plane crosses, do not run alone at the end
+    a.nsplit = std::max(1, std::min(32, n / 512));
+    if (a.nsplit > 1) {
+      int rc = ensure_scratch(c);
+      if (rc) return rc;
+      a.scratch = c->scratch;
+    }
     cudaError_t e = launch_gather(cfg.shape, cfg.wmode, a, st, 0, nullptr);
     if (e != cudaSuccess) return cuda_fail(e);
+    if (a.nsplit > 1) {
+      e = launch_merge_scratch(a, st);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
     return FR_OK;
   }
   int rc = ensure_scratch(c);
@@ -309,12 +321,17 @@ int fr_create(int S, const fr_blob *blob, fr_ctx **out) {
     double mono[POLY_N];
     chebyshev_power_basis(bx, mono);
     for (int k = 0; k < POLY_N; ++k) c->poly[k] = (float)mono[k];
-    // measured error of the FP32 Horner evaluation the device performs
+    // measured error of the FP32 even/odd evaluation the device performs
     double worst = 0;
     for (int i = 0; i <= 20000; ++i) {
       const float x = -1.0f + 2.0f * (float)i / 20000.0f;
-      float p = c->poly[POLY_N - 1];
-      for (int k = POLY_N - 2; k >= 0; --k) p = std::fma(p, x, c->poly[k]);
+      const float y = x * x;
+      float e = c->poly[POLY_N - 2], o = c->poly[POLY_N - 1];
+      for (int k = POLY_N / 2 - 2; k >= 0; --k) {
+        e = std::fma(e, y, c->poly[2 * k]);
+        o = std::fma(o, y, c->poly[2 * k + 1]);
+      }
+      const float p = std::fma(o, x, e);
       worst = std::max(worst, std::fabs((double)p - bx((double)x)));
     }
     c->poly_err = worst;
