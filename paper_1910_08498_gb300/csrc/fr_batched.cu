@@ -46,7 +46,13 @@ int insert_batched(fr_ctx *const *ctxs, const void *const *images, const int *dt
   }
   if (nb == 0) return FR_OK;
   std::vector<int> cfg(nb);
-  for (int b = 0; b < nb; ++b) cfg[b] = batched_config(ctxs[b], n[b], dtypes[b]);
+  for (int b = 0; b < nb; ++b) {
+    cfg[b] = batched_config(ctxs[b], n[b], dtypes[b]);
+    if (n[b] > 0) {
+      int rc = prepare_config(ctxs[b], cfg[b], n[b]);
+      if (rc != FR_OK) return rc;
+    }
+  }
   auto enqueue = [&]() -> int {
     for (int b = 0; b < nb; ++b) {
       if (n[b] == 0) continue;

@@ -28,6 +28,12 @@ struct fr_ctx {
   unsigned long long images = 0;
   int launches = 0;
   fr::Tuner tuner;
+  // gather work-unit lists, keyed by (brick shape, n); most recent first
+  struct Units {
+    int shape = -1, n = -1, count = 0, any_split = 0;
+    int4 *dev = nullptr;
+  };
+  Units units[8];
   // cost model
   float *d_mlp = nullptr;
   bool mlp_trained = false;

@@ -238,15 +238,16 @@ gather_kernel(const InsertArgs args) {
   auto LF = [&](int f, int i) -> float & { return s_list[f * lcap + i]; };
   auto LI = [&](int f, int i) -> int { return __float_as_int(s_list[f * lcap + i]); };
 
-  // this CTA's brick and image range, this warp's footprint (8 x 4 columns, ZC deep)
-  const int nbz = args.nbz;
-  const int bz = blockIdx.z % nbz, split = blockIdx.z / nbz;
-  const int img0 = (int)((long long)args.n * split / args.nsplit);
-  const int img1 = (int)((long long)args.n * (split + 1) / args.nsplit);
+  // this CTA's work unit (brick and share of the images), this warp's
+  // footprint (8 x 4 columns, ZC deep)
+  const int4 unit = args.units[blockIdx.x];
+  const int split = unit.w & 0xffff, nsplit = unit.w >> 16;
+  const int img0 = (int)((long long)args.n * split / nsplit);
+  const int img1 = (int)((long long)args.n * (split + 1) / nsplit);
   const int wx = warp % (BX / 8), wy = warp / (BX / 8);
-  const int fx0 = g.xa0 + blockIdx.x * BX + wx * 8;
-  const int fy0 = -g.H + blockIdx.y * BY + wy * 4;
-  const int z0 = -g.H + bz * ZC;
+  const int fx0 = g.xa0 + unit.x * BX + wx * 8;
+  const int fy0 = -g.H + unit.y * BY + wy * 4;
+  const int z0 = -g.H + unit.z * ZC;
   const float cx = fx0 + 3.5f, cy = fy0 + 1.5f, cz = z0 + 0.5f * (ZC - 1);  // footprint centre
   const float hz = 0.5f * (ZC - 1);
   const float rw = sqrtf(3.5f * 3.5f + 1.5f * 1.5f + hz * hz);
@@ -293,7 +294,7 @@ gather_kernel(const InsertArgs args) {
         const float ar = s_acc[lane * ZC + t], ai = s_acc[WV + lane * ZC + t],
                     aw = s_acc[2 * WV + lane * ZC + t];
         if (aw != 0.f || ar != 0.f || ai != 0.f) {
-          if (args.nsplit == 1) {
+          if (nsplit == 1) {
             const float add[3] = {ar, ai, aw};
 #pragma unroll
             for (int c = 0; c < 3; ++c) {

@@ -54,7 +54,9 @@ struct InsertArgs {
   // gather geometry
   int nbx, nby, nbz;    // bricks per axis
   int chunk;            // capacity of a warp's image list
-  int nsplit;           // CTAs per brick, each taking a contiguous share of the images
+  const int4 *units;    // work units: (brick x, y, z, split | nsplit << 16), one per CTA
+  int nunits;
+  int any_split;        // 1 if some unit shares its brick with other units
   // scatter
   float4 *scratch;      // [z][y][x - xa0] (re, im, w, 0)
 };

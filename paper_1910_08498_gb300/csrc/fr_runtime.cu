@@ -101,6 +101,80 @@ static int ensure_scratch(fr_ctx *c) {
   return FR_OK;
 }
 
+// Work units of a gather launch.  A brick at distance d from the centre is
+// crossed, within a + (brick radius) r, by a fraction min(1, (a + r) / d) of
+// uniformly oriented planes through the origin, so its expected image count is
+// n min(1, (a + r) / d).  Bricks whose count exceeds a target share are split
+// into several units, each taking a contiguous range of the images, and units
+// are ordered heaviest first so the largest ones start first.
+static int gather_units(fr_ctx *c, const Config &cfg, int n, InsertArgs &a) {
+  for (int k = 0; k < 8; ++k) {
+    fr_ctx::Units &u = c->units[k];
+    if (u.dev && u.shape == cfg.shape && u.n == n) {
+      a.units = u.dev;
+      a.nunits = u.count;
+      a.any_split = u.any_split;
+      return FR_OK;
+    }
+  }
+  const GatherShape sh = gather_shape(cfg.shape);
+  const Geom &g = c->g;
+  const int nbx = (g.NXa + sh.bx - 1) / sh.bx, nby = (g.D + sh.by - 1) / sh.by,
+            nbz = (g.D + sh.zc - 1) / sh.zc;
+  const double hx = 0.5 * (sh.bx - 1), hy = 0.5 * (sh.by - 1), hz = 0.5 * (sh.zc - 1);
+  const double rb = std::sqrt(hx * hx + hy * hy + hz * hz);
+  const double reach = std::sqrt(2.0) * (g.H + g.a) + rb;
+  std::vector<double> load((size_t)nbx * nby * nbz);
+  double total = 0;
+  for (int bz = 0; bz < nbz; ++bz)
+    for (int by = 0; by < nby; ++by)
+      for (int bx = 0; bx < nbx; ++bx) {
+        const double cx = g.xa0 + bx * sh.bx + hx, cy = -g.H + by * sh.by + hy,
+                     cz = -g.H + bz * sh.zc + hz;
+        const double d = std::sqrt(cx * cx + cy * cy + cz * cz);
+        double f = d <= g.a + rb ? 1.0 : (g.a + rb) / d;
+        if (d - rb > reach) f = 0.0;
+        const double l = n * f + 0.02 * n;  // images kept, plus the cull scan
+        load[((size_t)bz * nby + by) * nbx + bx] = l;
+        total += l;
+      }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const double target = std::max(64.0, total / (std::max(sms, 1) * 8.0));
+  struct U { double w; int4 v; };
+  std::vector<U> us;
+  us.reserve(load.size() + 64);
+  int any_split = 0;
+  for (int bz = 0; bz < nbz; ++bz)
+    for (int by = 0; by < nby; ++by)
+      for (int bx = 0; bx < nbx; ++bx) {
+        const double l = load[((size_t)bz * nby + by) * nbx + bx];
+        int ns = (int)std::ceil(l / target);
+        ns = std::max(1, std::min(ns, std::min(64, std::max(1, n / 32))));
+        if (ns > 1) any_split = 1;
+        for (int s = 0; s < ns; ++s) us.push_back(U{l / ns, make_int4(bx, by, bz, s | (ns << 16))});
+      }
+  std::stable_sort(us.begin(), us.end(), [](const U &p, const U &q) { return p.w > q.w; });
+  std::vector<int4> host(us.size());
+  for (size_t i = 0; i < us.size(); ++i) host[i] = us[i].v;
+  // replace the oldest cached list
+  fr_ctx::Units &slot = c->units[7];
+  cudaFree(slot.dev);
+  for (int k = 7; k > 0; --k) c->units[k] = c->units[k - 1];
+  c->units[0] = fr_ctx::Units{};
+  fr_ctx::Units &u = c->units[0];
+  FR_CUDA(cudaMalloc(&u.dev, host.size() * sizeof(int4)));
+  FR_CUDA(cudaMemcpy(u.dev, host.data(), host.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  u.shape = cfg.shape;
+  u.n = n;
+  u.count = (int)host.size();
+  u.any_split = any_split;
+  a.units = u.dev;
+  a.nunits = u.count;
+  a.any_split = any_split;
+  return FR_OK;
+}
+
 // Fill the launch geometry of configuration `cfg` into `a`.
 static void gather_geometry(const fr_ctx *c, const Config &cfg, InsertArgs &a) {
   GatherShape sh = gather_shape(cfg.shape);
@@ -108,6 +182,19 @@ static void gather_geometry(const fr_ctx *c, const Config &cfg, InsertArgs &a) {
   a.nbx = (c->g.NXa + sh.bx - 1) / sh.bx;
   a.nby = (c->g.D + sh.by - 1) / sh.by;
   a.nbz = (c->g.D + sh.zc - 1) / sh.zc;
+}
+
+// Allocate and upload whatever a launch of configuration id on n images
+// needs (work units, scratch), so that the launch itself only enqueues work.
+int prepare_config(fr_ctx *c, int id, int n) {
+  const Config &cfg = config_space()[id];
+  InsertArgs a = base_args(c);
+  if (cfg.algo == ALGO_GATHER) {
+    int rc = gather_units(c, cfg, n, a);
+    if (rc) return rc;
+    return a.any_split ? ensure_scratch(c) : FR_OK;
+  }
+  return ensure_scratch(c);
 }
 
 // Enqueue the insertion of n images with configuration id; no timing.
@@ -121,17 +208,16 @@ int run_config(fr_ctx *c, int id, const void *images, int f16, const float *rot,
   a.n = n;
   if (cfg.algo == ALGO_GATHER) {
     gather_geometry(c, cfg, a);
-    // split the images of large batches across several CTAs per brick so the
-    // bricks at the centre, which every plane crosses, do not run alone at the end
-    a.nsplit = std::max(1, std::min(32, n / 512));
-    if (a.nsplit > 1) {
-      int rc = ensure_scratch(c);
+    int rc = gather_units(c, cfg, n, a);
+    if (rc) return rc;
+    if (a.any_split) {
+      rc = ensure_scratch(c);
       if (rc) return rc;
       a.scratch = c->scratch;
     }
     cudaError_t e = launch_gather(cfg.shape, cfg.wmode, a, st, 0, nullptr);
     if (e != cudaSuccess) return cuda_fail(e);
-    if (a.nsplit > 1) {
+    if (a.any_split) {
       e = launch_merge_scratch(a, st);
       if (e != cudaSuccess) return cuda_fail(e);
     }
@@ -352,6 +438,7 @@ int fr_destroy(fr_ctx *c) {
   cudaFree(c->d_err);
   cudaFree(c->d_count);
   cudaFree(c->d_mlp);
+  for (auto &u : c->units) cudaFree(u.dev);
   delete c;
   return FR_OK;
 }

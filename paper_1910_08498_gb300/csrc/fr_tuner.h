@@ -46,6 +46,7 @@ int default_config(const fr_ctx *c);
 int config_valid(const fr_ctx *c, int id);
 int run_config(fr_ctx *c, int id, const void *images, int f16, const float *rot, int n,
                cudaStream_t st);
+int prepare_config(fr_ctx *c, int id, int n);
 
 // Eq. (performance), Eq. (invocations), Eq. (samples) of Sec. 5.4
 double relative_performance(double s, double t_avg, double t_well, double n);

@@ -23,6 +23,17 @@ def rel_err(x_gpu, x_ref):
     return float(np.max(np.abs(x_gpu - x_ref)) / den) if den > 0 else float(np.max(np.abs(x_gpu)))
 
 
+def worst(x_gpu, x_ref, S):
+    """Description of the worst voxel (coordinates, values) for failure messages."""
+    x_gpu = np.asarray(x_gpu).ravel()
+    x_ref = np.asarray(x_ref).ravel()
+    i = int(np.argmax(np.abs(x_gpu - x_ref)))
+    D, H = S + 1, S // 2
+    z, r = divmod(i, D * D)
+    y, x = divmod(r, D)
+    return f"worst voxel (x,y,z)=({x - H},{y - H},{z - H}) gpu={x_gpu[i]} ref={x_ref[i]}"
+
+
 def sym_np(V, W, S):
     D = S + 1
     V = V.reshape(D, D, D)
