@@ -92,6 +92,39 @@ __device__ __forceinline__ void dd_add2(float &hi, float &lo, float xh, float xl
   lo = e - (hi - s);
 }
 
+// Exact decision of |v - (kx e1 + ky e2)|^2 <= a^2 for integer v, k and
+// binary32 e1, e2, a, in double-float arithmetic (error-free products and
+// sums): the result differs from the real-number decision only if the two
+// sides agree to ~2^-44 relative.  Used to re-decide candidates whose FP32 r^2
+// lies within rounding of a^2 -- with a non-orthonormal FP32 rotation and an
+// integer a^2, |R k| may sit a few ulps either side of a lattice distance.
+static __device__ __noinline__ bool exact_r2_le_a2(int vx, int vy, int vz, float e1x, float e1y,
+                                            float e1z, float e2x, float e2y, float e2z, int kx,
+                                            int ky, float a) {
+  const float e1[3] = {e1x, e1y, e1z}, e2[3] = {e2x, e2y, e2z};
+  const int v[3] = {vx, vy, vz};
+  float rh = 0.f, rl = 0.f;  // running r^2 as hi + lo
+  for (int c = 0; c < 3; ++c) {
+    // d = v_c - e1_c kx - e2_c ky
+    const float p1 = e1[c] * (float)kx, x1 = fmaf(e1[c], (float)kx, -p1);
+    const float p2 = e2[c] * (float)ky, x2 = fmaf(e2[c], (float)ky, -p2);
+    float s, t, s2, t2;
+    two_sum((float)v[c], -p1, s, t);
+    two_sum(s, -p2, s2, t2);
+    const float dl = ((t + t2) - x1) - x2;
+    // d^2 = s2^2 + 2 s2 dl (+ dl^2, negligible)
+    const float q = s2 * s2, qe = fmaf(s2, s2, -q);
+    float h, e;
+    two_sum(rh, q, h, e);
+    rh = h;
+    rl += e + qe + 2.0f * s2 * dl;
+  }
+  const float ah = a * a, al = fmaf(a, a, -ah);
+  float dh, de;
+  two_sum(rh, -ah, dh, de);
+  return dh + (de + (rl - al)) <= 0.0f;
+}
+
 // ---------------------------------------------------------------- blob weights
 
 // Tabulated blob: nodes at r^2 = i a^2 / (lut_n - 1), linear interpolation in

@@ -168,10 +168,12 @@ __device__ __forceinline__ void box_fast_poly(const InsertArgs &args, const floa
 // range tests per pixel; the W weight counts each contribution.
 template <int WMODE, int KB, int F16>
 __device__ __noinline__ void box_careful(const InsertArgs &args, const float2 *lut,
-                                         const unsigned char *ibase, float r00, float r01,
+                                         const unsigned char *ibase, const float *e,
                                          int kx0, int ky0, float fx, float fy, float uz2,
-                                         bool fold_check, float vr2, float inv_a2, float &sr,
-                                         float &si, float &sw) {
+                                         bool fold_check, int vx, int vy, int vz, float inv_a2,
+                                         float &sr, float &si, float &sw) {
+  const float r00 = e[0], r01 = e[3];  // e = (e1x, e1y, e1z, e2x, e2y, e2z)
+  const float vr2 = (float)(vx * vx + vy * vy + vz * vz);
   const Geom &g = args.g;
   constexpr int ESZ = F16 ? 4 : 8;
   for (int l = 0; l < KB; ++l) {
@@ -185,7 +187,12 @@ __device__ __noinline__ void box_careful(const InsertArgs &args, const float2 *l
       // |v|^2 so that a lattice voxel at distance exactly a is decided as the
       // definition decides it
       const float r2 = (cx == 0 && cy == 0) ? vr2 : fmaf(dx, dx, ry);
-      if (!(r2 <= g.a2)) continue;
+      // within rounding of the blob edge: decide as the real numbers do
+      if (fabsf(r2 - g.a2) <= 1e-5f * g.a2 && !(cx == 0 && cy == 0)) {
+        if (!exact_r2_le_a2(vx, vy, vz, e[0], e[1], e[2], e[3], e[4], e[5], cx, cy, g.a)) continue;
+      } else if (!(r2 <= g.a2)) {
+        continue;
+      }
       const float w = blob_w<WMODE>(lut, r2, args, inv_a2);
       // stored pixel c, not folded
       if (cx >= 0 && cx <= g.H && cy >= -g.H && cy < g.H &&
@@ -340,9 +347,10 @@ gather_kernel(const InsertArgs args) {
         box_fast<WMODE, KB, F16>(args, lut, ibase, sgn, kx0, ky0, fx, fy, uz2, inv_a2, sr, si, sw);
       si *= (float)sgn;
     } else {
-      const float vr2 = (float)(sx * sx + sy * sy + sz * sz);
-      box_careful<WMODE, KB, F16>(args, lut, ibase, LF(LF_E1X, li), LF(LF_E2X, li), kx0, ky0, fx,
-                                  fy, uz2, sx <= -g.xa0, vr2, inv_a2, sr, si, sw);
+      const float e[6] = {LF(LF_E1X, li), LF(LF_E1Y, li), LF(LF_E1Z, li),
+                          LF(LF_E2X, li), LF(LF_E2Y, li), LF(LF_E2Z, li)};
+      box_careful<WMODE, KB, F16>(args, lut, ibase, e, kx0, ky0, fx, fy, uz2, sx <= -g.xa0, sx,
+                                  sy, sz, inv_a2, sr, si, sw);
     }
     const int slot = src * ZC + t;
     atomicAdd(&s_acc[slot], sr);

@@ -52,31 +52,42 @@ __global__ void scatter_kernel(const InsertArgs args) {
     rk_dd(R00, R01, (float)kx, (float)ky, qxh, qxl);
     rk_dd(R10, R11, (float)kx, (float)ky, qyh, qyl);
     rk_dd(R20, R21, (float)kx, (float)ky, qzh, qzl);
-    if (fold_pred(R00, R01, kx, ky)) {
+    const bool folded = fold_pred(R00, R01, kx, ky);
+    if (folded) {
       qxh = -qxh; qxl = -qxl; qyh = -qyh; qyl = -qyl; qzh = -qzh; qzl = -qzl; p.y = -p.y;
     }
-    const int x0 = (int)ceilf((qxh + qxl) - a);
-    const int y0 = (int)ceilf((qyh + qyl) - a);
-    const int z0 = (int)ceilf((qzh + qzl) - a);
+    // box origin shifted down by a small margin when the box has a spare cell,
+    // so a voxel at distance exactly a is never lost to rounding of q
+    const float a_box = KB > (int)floorf(2.0f * a) + 1 ? a + 1e-4f : a;
+    const int x0 = (int)ceilf((qxh + qxl) - a_box);
+    const int y0 = (int)ceilf((qyh + qyl) - a_box);
+    const int z0 = (int)ceilf((qzh + qzl) - a_box);
 #pragma unroll 1
     for (int dz = 0; dz < KB; ++dz) {
       const int z = z0 + dz;
       const float fz = ((float)z - qzh) - qzl;
       const float rz = fz * fz;
-      if (z < -g.H || z > g.H || rz > a2) continue;
+      if (z < -g.H || z > g.H || rz > a2 * (1.0f + 2e-5f)) continue;
 #pragma unroll 1
       for (int dy = 0; dy < KB; ++dy) {
         const int y = y0 + dy;
         const float fy = ((float)y - qyh) - qyl;
         const float ryz = fmaf(fy, fy, rz);
-        if (y < -g.H || y > g.H || ryz > a2) continue;
+        if (y < -g.H || y > g.H || ryz > a2 * (1.0f + 2e-5f)) continue;
         float4 *rowp = args.scratch + ((size_t)(z + g.H) * g.D + (size_t)(y + g.H)) * g.NXa - g.xa0;
 #pragma unroll
         for (int dx = 0; dx < KB; ++dx) {
           const int x = x0 + dx;
           const float fx = ((float)x - qxh) - qxl;
           const float r2 = fmaf(fx, fx, ryz);
-          if (r2 <= a2 && x <= g.H && x >= g.xa0) {
+          bool in = r2 <= a2;
+          if (fabsf(r2 - a2) <= 1e-5f * a2) {
+            // within rounding of the blob edge: decide as the real numbers do
+            const float sg = folded ? -1.f : 1.f;
+            in = exact_r2_le_a2(x, y, z, sg * R00, sg * R10, sg * R20, sg * R01, sg * R11,
+                                sg * R21, kx, ky, a);
+          }
+          if (in && x <= g.H && x >= g.xa0) {
             const float w = blob_w<WMODE>(s_lut, r2, args, inv_a2);
             atomicAdd(rowp + x, make_float4(w * p.x, w * p.y, w, 0.f));
           }

@@ -140,7 +140,7 @@ static int gather_units(fr_ctx *c, const Config &cfg, int n, InsertArgs &a) {
       }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  const double target = std::max(64.0, total / (std::max(sms, 1) * 8.0));
+  const double target = std::max(64.0, total / (std::max(sms, 1) * 32.0));
   struct U { double w; int4 v; };
   std::vector<U> us;
   us.reserve(load.size() + 64);
