@@ -125,7 +125,9 @@ __device__ __forceinline__ void box_fast(const InsertArgs &args, const float2 *l
 // masked to 0 outside r <= a, so all lanes stay converged.  The polynomial is
 // split into even and odd parts, E(x^2) + x O(x^2), evaluated together with
 // packed FP32x2 FMAs (c holds (c_0, c_1), (c_2, c_3), ... pairs).
-template <int KB, int F16>
+// EDGE: the box may cross the image border; rows and columns outside the
+// stored (or mirrored) pixels get weight 0 and read a clamped, valid pixel.
+template <int KB, int F16, bool EDGE>
 __device__ __forceinline__ void box_fast_poly(const InsertArgs &args, const float2 *c,
                                               const unsigned char *ibase, int sgn, int kx0,
                                               int ky0, float fx, float fy, float uz2,
@@ -136,6 +138,19 @@ __device__ __forceinline__ void box_fast_poly(const InsertArgs &args, const floa
   constexpr int NP = POLY_N / 2;
   const int row_bytes = g.NX * ESZ;
   const int step = sgn * ESZ;
+  // valid pixel columns pc = sgn (kx0 + j) in [1, H]
+  unsigned colok = (1u << KB) - 1u;
+  int jsafe = 0;  // a valid column, read in place of the invalid ones
+  if (EDGE) {
+    colok = 0;
+#pragma unroll
+    for (int j = 0; j < KB; ++j) {
+      const int pc = sgn * (kx0 + j);
+      colok |= (pc >= 1 && pc <= g.H ? 1u : 0u) << j;
+    }
+    if (!colok) return;
+    jsafe = __ffs(colok) - 1;
+  }
   float2 acc = make_float2(sr, si);
 #pragma unroll 1
   for (int l = 0; l < KB; ++l) {
@@ -143,6 +158,7 @@ __device__ __forceinline__ void box_fast_poly(const InsertArgs &args, const floa
     const float ry = fmaf(dy, dy, uz2);
     if (ry > g.a2) continue;
     int ky = sgn * (ky0 + l);
+    if (EDGE && (ky < -g.H || ky >= g.H)) continue;
     ky += ky < 0 ? g.S : 0;
     const unsigned char *row = ibase + (ky * row_bytes + sgn * kx0 * ESZ);
 #pragma unroll
@@ -154,8 +170,10 @@ __device__ __forceinline__ void box_fast_poly(const InsertArgs &args, const floa
       float2 eo = c[NP - 1];
 #pragma unroll
       for (int k = NP - 2; k >= 0; --k) eo = __ffma2_rn(eo, make_float2(x2, x2), c[k]);
-      const float w = r2 <= g.a2 ? fmaf(eo.y, x, eo.x) : 0.0f;
-      const float2 p = ld_px<F16>(row + j * step);
+      const bool ok = EDGE ? ((colok >> j) & 1u) != 0 : true;
+      const float w = (r2 <= g.a2 && ok) ? fmaf(eo.y, x, eo.x) : 0.0f;
+      const int off = (EDGE && !ok ? jsafe : j) * step;
+      const float2 p = ld_px<F16>(row + off);
       acc = __ffma2_rn(make_float2(w, w), p, acc);
       sw += w;
     }
@@ -235,12 +253,13 @@ gather_kernel(const InsertArgs args) {
   unsigned char *sp = smem;
   float2 *s_lut = reinterpret_cast<float2 *>(sp);
   if (WMODE == W_LUT) sp += ((size_t)args.lut_n * sizeof(float2) + 15) & ~(size_t)15;
-  const size_t per_warp = (size_t)LIST_FIELDS * lcap * 4 + (size_t)3 * WV * 4 + (size_t)2 * QCAP * 4;
+  const size_t per_warp = (size_t)LIST_FIELDS * lcap * 4 + (size_t)3 * WV * 4 + (size_t)3 * QCAP * 4;
   sp += (size_t)warp * per_warp;
   float *s_list = reinterpret_cast<float *>(sp);         // [LIST_FIELDS][lcap]
   float *s_acc = s_list + (size_t)LIST_FIELDS * lcap;   // [3][WV]
   unsigned *s_qf = reinterpret_cast<unsigned *>(s_acc + 3 * WV);  // fast items
-  unsigned *s_qc = s_qf + QCAP;                                    // careful items
+  unsigned *s_qe = s_qf + QCAP;                                    // fast items at the image edge
+  unsigned *s_qc = s_qe + QCAP;                                    // careful items
   const float2 *lut = s_lut;
   auto LF = [&](int f, int i) -> float & { return s_list[f * lcap + i]; };
   auto LI = [&](int f, int i) -> int { return __float_as_int(s_list[f * lcap + i]); };
@@ -325,7 +344,7 @@ gather_kernel(const InsertArgs args) {
 
   // one queued (image, voxel) item: form the box sums and add them to the
   // warp's partial sums
-  auto process = [&](unsigned it, bool careful) {
+  auto process = [&](unsigned it, int kind) {  // 0 fast, 1 fast at the image edge, 2 careful
     const int li = (int)(it >> 9), src = (int)((it >> 3) & 31), t = (int)(it & 7);
     const int sgn = (it >> 8) & 1 ? -1 : 1;
     const int sx = fx0 + (src & 7), sy = fy0 + (src >> 3), sz = z0 + t;
@@ -339,12 +358,17 @@ gather_kernel(const InsertArgs args) {
     const float uz2 = uz * uz;
     const unsigned char *ibase = imgs + (size_t)LI(LF_IMG, li) * img_stride;
     float sr = 0.f, si = 0.f, sw = 0.f;
-    if (!careful) {
-      if (WMODE == W_POLY)
-        box_fast_poly<KB, F16>(args, cpair, ibase, sgn, kx0, ky0, fx, fy, uz2, 2.0f * inv_a2, sr,
-                               si, sw);
-      else
+    if (kind == 0 || (kind == 1 && WMODE == W_POLY)) {
+      if (WMODE == W_POLY) {
+        if (kind == 0)
+          box_fast_poly<KB, F16, false>(args, cpair, ibase, sgn, kx0, ky0, fx, fy, uz2,
+                                        2.0f * inv_a2, sr, si, sw);
+        else
+          box_fast_poly<KB, F16, true>(args, cpair, ibase, sgn, kx0, ky0, fx, fy, uz2,
+                                       2.0f * inv_a2, sr, si, sw);
+      } else {
         box_fast<WMODE, KB, F16>(args, lut, ibase, sgn, kx0, ky0, fx, fy, uz2, inv_a2, sr, si, sw);
+      }
       si *= (float)sgn;
     } else {
       const float e[6] = {LF(LF_E1X, li), LF(LF_E1Y, li), LF(LF_E1Z, li),
@@ -360,10 +384,10 @@ gather_kernel(const InsertArgs args) {
 
   // drain full rounds of 32 items (all of them if `all`); the remainder moves
   // to the front of the queue
-  auto drain = [&](unsigned *q, int &qlen, bool careful, bool all) {
+  auto drain = [&](unsigned *q, int &qlen, int kind, bool all) {
     __syncwarp();
     const int nfull = all ? qlen : (qlen & ~31);
-    for (int k = lane; k < nfull; k += 32) process(q[k], careful);
+    for (int k = lane; k < nfull; k += 32) process(q[k], kind);
     __syncwarp();
     const int rest = qlen - nfull;
     if (rest) {
@@ -376,8 +400,8 @@ gather_kernel(const InsertArgs args) {
   };
 
   // queue the footprint's voxels near the plane of list entry li that the
-  // extended plane reaches, fast and careful ones apart
-  int qf = 0, qc = 0;
+  // extended plane reaches: fast, fast at the image edge, and careful apart
+  int qf = 0, qe = 0, qc = 0;
   auto enqueue = [&](int li) {
     const float mx = LF(LF_MX, li), my = LF(LF_MY, li), mz = LF(LF_MZ, li);
     const float bz = fmaf(my, dvy, fmaf(mx, dvx, LF(LF_UZ, li)));
@@ -385,7 +409,7 @@ gather_kernel(const InsertArgs args) {
     const float by = fmaf(LF(LF_E2Y, li), dvy, fmaf(LF(LF_E2X, li), dvx, LF(LF_FY, li)));
     const int cix = LI(LF_CIX, li), ciy = LI(LF_CIY, li);
     const float e1z = LF(LF_E1Z, li), e2z = LF(LF_E2Z, li);
-    unsigned mf = 0, mc = 0, mneg = 0;
+    unsigned mf = 0, me = 0, mc = 0, mneg = 0;
 #pragma unroll
     for (int t = 0; t < ZC; ++t) {
       const float dz = (float)(z0 + t) - cz;
@@ -394,19 +418,21 @@ gather_kernel(const InsertArgs args) {
       const float ux = (float)cix + uxr, uy = (float)ciy + uyr;
       if (fabsf(uz) <= a_plane && fabsf(ux) <= reach && fabsf(uy) <= reach) {
         const int kx0 = cix + (int)ceilf(uxr - a_box), ky0 = ciy + (int)ceilf(uyr - a_box);
-        const bool direct = kx0 >= 1 && kx0 + KB - 1 <= g.H && ky0 >= -g.H && ky0 + KB - 1 < g.H;
-        const bool mirror = kx0 + KB - 1 <= -1 && kx0 >= -g.H && ky0 > -g.H && ky0 + KB - 1 <= g.H;
+        const bool direct = kx0 >= 1, mirror = kx0 + KB - 1 <= -1;
         if (!fold_col && (direct || mirror)) {
-          mf |= 1u << t;
+          const bool interior = direct
+              ? (kx0 + KB - 1 <= g.H && ky0 >= -g.H && ky0 + KB - 1 < g.H)
+              : (kx0 >= -g.H && ky0 > -g.H && ky0 + KB - 1 <= g.H);
+          if (interior) mf |= 1u << t; else me |= 1u << t;
           if (mirror) mneg |= 1u << t;
         } else {
           mc |= 1u << t;
         }
       }
     }
-    if (!col_in) mf = mc = 0;
-    // warp prefix sums of both counts (packed 16 + 16 bits)
-    const int cnt = __popc(mf) | (__popc(mc) << 16);
+    if (!col_in) mf = me = mc = 0;
+    // warp prefix sums of the three counts (packed 10 bits each)
+    const int cnt = __popc(mf) | (__popc(me) << 10) | (__popc(mc) << 20);
     int incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -415,22 +441,29 @@ gather_kernel(const InsertArgs args) {
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     const int excl = incl - cnt;
-    int pf = qf + (excl & 0xffff), pc = qc + (excl >> 16);
+    int pf = qf + (excl & 1023), pe = qe + ((excl >> 10) & 1023), pc = qc + (excl >> 20);
     const unsigned base = ((unsigned)li << 9) | ((unsigned)lane << 3);
     while (mf) {
       const int t = __ffs(mf) - 1;
       mf &= mf - 1;
       s_qf[pf++] = base | (((mneg >> t) & 1u) << 8) | (unsigned)t;
     }
+    while (me) {
+      const int t = __ffs(me) - 1;
+      me &= me - 1;
+      s_qe[pe++] = base | (((mneg >> t) & 1u) << 8) | (unsigned)t;
+    }
     while (mc) {
       const int t = __ffs(mc) - 1;
       mc &= mc - 1;
       s_qc[pc++] = base | (unsigned)t;
     }
-    qf += total & 0xffff;
-    qc += total >> 16;
-    if (qf >= 32) drain(s_qf, qf, false, false);
-    if (qc >= 32) drain(s_qc, qc, true, false);
+    qf += total & 1023;
+    qe += (total >> 10) & 1023;
+    qc += total >> 20;
+    if (qf >= 32) drain(s_qf, qf, 0, false);
+    if (qe >= 32) drain(s_qe, qe, 1, false);
+    if (qc >= 32) drain(s_qc, qc, 2, false);
   };
 
   const float *rot = args.rot;
@@ -440,15 +473,17 @@ gather_kernel(const InsertArgs args) {
     for (int li = 0; li < nl; ++li) {
       enqueue(li);
       if (++since_flush >= GATHER_FLUSH) {
-        drain(s_qf, qf, false, true);
-        drain(s_qc, qc, true, true);
+        drain(s_qf, qf, 0, true);
+        drain(s_qe, qe, 1, true);
+        drain(s_qc, qc, 2, true);
         flush();
         since_flush = 0;
       }
     }
     // the list is rebuilt next: nothing may refer to it afterwards
-    drain(s_qf, qf, false, true);
-    drain(s_qc, qc, true, true);
+    drain(s_qf, qf, 0, true);
+    drain(s_qe, qe, 1, true);
+    drain(s_qc, qc, 2, true);
     nl = 0;
   };
 

@@ -30,7 +30,7 @@ size_t gather_smem_bytes(const GatherShape &sh, int wmode, int lut_n, int chunk)
   size_t b = 0;
   if (wmode == W_LUT) b += up16((size_t)lut_n * sizeof(float2));
   // per warp: image list, partial sums, item queue
-  b += (size_t)nw * ((size_t)LIST_FIELDS * chunk * 4 + (size_t)3 * wv * 4 + (size_t)2 * (wv + 32) * 4);
+  b += (size_t)nw * ((size_t)LIST_FIELDS * chunk * 4 + (size_t)3 * wv * 4 + (size_t)3 * (wv + 32) * 4);
   return b;
 }
 
