@@ -285,7 +285,6 @@ gather_kernel(const InsertArgs args) {
   // never lost to rounding of u; the r^2 <= a^2 test decides it.
   const float a_box = KB > (int)floorf(2.0f * a) + 1 ? a + 1e-4f : a;
   const float a_plane = a + 1e-4f;  // conservative |u_z| <= a test for queueing
-  const float cull = a + rw + 1e-3f;
   const float reach = (float)g.H + a;  // the extended plane spans [-H, H]^2
   const float ext = reach + rw + 1.0f;
   const int vx = fx0 + (lane & 7), vy = fy0 + (lane >> 3);
@@ -409,14 +408,23 @@ gather_kernel(const InsertArgs args) {
     const float by = fmaf(LF(LF_E2Y, li), dvy, fmaf(LF(LF_E2X, li), dvx, LF(LF_FY, li)));
     const int cix = LI(LF_CIX, li), ciy = LI(LF_CIY, li);
     const float e1z = LF(LF_E1Z, li), e2z = LF(LF_E2Z, li);
-    unsigned mf = 0, me = 0, mc = 0, mneg = 0;
+    // phase 1: voxels of this column within a of the plane (cheap, all lanes)
+    unsigned near = 0;
 #pragma unroll
     for (int t = 0; t < ZC; ++t) {
+      const float uz = fmaf(mz, (float)(z0 + t) - cz, bz);
+      near |= (fabsf(uz) <= a_plane ? 1u : 0u) << t;
+    }
+    if (!col_in) near = 0;
+    if (!__any_sync(0xffffffffu, near != 0)) return;
+    // phase 2: classify only those
+    unsigned mf = 0, me = 0, mc = 0, mneg = 0;
+    for (unsigned m = near; m; m &= m - 1) {
+      const int t = __ffs(m) - 1;
       const float dz = (float)(z0 + t) - cz;
-      const float uz = fmaf(mz, dz, bz);
       const float uxr = fmaf(e1z, dz, bx), uyr = fmaf(e2z, dz, by);
       const float ux = (float)cix + uxr, uy = (float)ciy + uyr;
-      if (fabsf(uz) <= a_plane && fabsf(ux) <= reach && fabsf(uy) <= reach) {
+      if (fabsf(ux) <= reach && fabsf(uy) <= reach) {
         const int kx0 = cix + (int)ceilf(uxr - a_box), ky0 = ciy + (int)ceilf(uyr - a_box);
         const bool direct = kx0 >= 1, mirror = kx0 + KB - 1 <= -1;
         if (!fold_col && (direct || mirror)) {
@@ -430,7 +438,6 @@ gather_kernel(const InsertArgs args) {
         }
       }
     }
-    if (!col_in) mf = me = mc = 0;
     // warp prefix sums of the three counts (packed 10 bits each)
     const int cnt = __popc(mf) | (__popc(me) << 10) | (__popc(mc) << 20);
     int incl = cnt;
@@ -500,7 +507,10 @@ gather_kernel(const InsertArgs args) {
       const float d = mx * cx + my * cy + mz * cz;
       const float ux = e1x * cx + e1y * cy + e1z * cz;
       const float uy = e2x * cx + e2y * cy + e2z * cz;
-      keep = col_in_any(g, fx0, fy0) && fabsf(d) <= cull && fabsf(ux) <= ext && fabsf(uy) <= ext;
+      // the plane's distance to the footprint box is |d| minus its support
+      const float supp = fabsf(mx) * 3.5f + fabsf(my) * 1.5f + fabsf(mz) * hz;
+      keep = col_in_any(g, fx0, fy0) && fabsf(d) <= a + supp + 1e-3f && fabsf(ux) <= ext &&
+             fabsf(uy) <= ext;
     }
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
     if (keep) {
