@@ -120,66 +120,101 @@ __device__ __forceinline__ void box_fast(const InsertArgs &args, const float2 *l
   }
 }
 
-// Branch-free fast box for the polynomial weights: every candidate of the
-// KB x KB box is evaluated (the pixels of a fast box all exist), the weight is
-// masked to 0 outside r <= a, so all lanes stay converged.  The polynomial is
-// split into even and odd parts, E(x^2) + x O(x^2), evaluated together with
-// packed FP32x2 FMAs (c holds (c_0, c_1), (c_2, c_3), ... pairs).
-// EDGE: the box may cross the image border; rows and columns outside the
-// stored (or mirrored) pixels get weight 0 and read a clamped, valid pixel.
-template <int KB, int F16, bool EDGE>
-__device__ __forceinline__ void box_fast_poly(const InsertArgs &args, const float2 *c,
+// Branch-free fast boxes for the polynomial weights.  The polynomial is split
+// into even and odd parts, E(x^2) + x O(x^2), evaluated together with packed
+// FP32x2 FMAs (c holds (c_0, c_1), (c_2, c_3), ... pairs).
+__device__ __forceinline__ float poly_eo(const float2 *c, float x) {
+  constexpr int NP = POLY_N / 2;
+  const float x2 = x * x;
+  float2 eo = c[NP - 1];
+#pragma unroll
+  for (int k = NP - 2; k >= 0; --k) eo = __ffma2_rn(eo, make_float2(x2, x2), c[k]);
+  return fmaf(eo.y, x, eo.x);
+}
+
+// Interior box: every pixel of the KB x KB box exists, so all candidates are
+// evaluated with no branch at all; weights outside r <= a are masked to 0.
+template <int KB, int F16>
+__device__ __forceinline__ void box_poly_interior(const InsertArgs &args, const float2 *c,
+                                                  const unsigned char *ibase, int sgn, int kx0,
+                                                  int ky0, float fx, float fy, float uz2,
+                                                  float two_inv_a2, float &sr, float &si,
+                                                  float &sw) {
+  const Geom &g = args.g;
+  constexpr int ESZ = F16 ? 4 : 8;
+  const int row_bytes = g.NX * ESZ;
+  const int step = sgn * ESZ;
+  const int col0 = sgn * kx0 * ESZ;
+  float ar = sr, ai = si, aw = sw;
+#pragma unroll
+  for (int l = 0; l < KB; ++l) {
+    const float dy = fy - (float)l;
+    const float ry = fmaf(dy, dy, uz2);
+    int ky = sgn * (ky0 + l);
+    ky += ky < 0 ? g.S : 0;
+    const unsigned char *row = ibase + (ky * row_bytes + col0);
+#pragma unroll
+    for (int j = 0; j < KB; ++j) {
+      const float dx = fx - (float)j;
+      const float r2 = fmaf(dx, dx, ry);
+      const float pv = poly_eo(c, fmaf(r2, two_inv_a2, -1.0f));
+      const float w = r2 <= g.a2 ? pv : 0.0f;
+      const float2 p = ld_px<F16>(row + j * step);
+      ar = fmaf(w, p.x, ar);
+      ai = fmaf(w, p.y, ai);
+      aw += w;
+    }
+  }
+  sr = ar;
+  si = ai;
+  sw = aw;
+}
+
+// Edge box: the box crosses the image border; rows and columns outside the
+// stored (or mirrored) pixels get weight 0 and read a valid pixel instead.
+template <int KB, int F16>
+__device__ __forceinline__ void box_poly_edge(const InsertArgs &args, const float2 *c,
                                               const unsigned char *ibase, int sgn, int kx0,
                                               int ky0, float fx, float fy, float uz2,
                                               float two_inv_a2, float &sr, float &si,
                                               float &sw) {
   const Geom &g = args.g;
   constexpr int ESZ = F16 ? 4 : 8;
-  constexpr int NP = POLY_N / 2;
   const int row_bytes = g.NX * ESZ;
   const int step = sgn * ESZ;
-  // valid pixel columns pc = sgn (kx0 + j) in [1, H]
-  unsigned colok = (1u << KB) - 1u;
-  int jsafe = 0;  // a valid column, read in place of the invalid ones
-  if (EDGE) {
-    colok = 0;
+  unsigned colok = 0;  // valid pixel columns pc = sgn (kx0 + j) in [1, H]
 #pragma unroll
-    for (int j = 0; j < KB; ++j) {
-      const int pc = sgn * (kx0 + j);
-      colok |= (pc >= 1 && pc <= g.H ? 1u : 0u) << j;
-    }
-    if (!colok) return;
-    jsafe = __ffs(colok) - 1;
+  for (int j = 0; j < KB; ++j) {
+    const int pc = sgn * (kx0 + j);
+    colok |= (pc >= 1 && pc <= g.H ? 1u : 0u) << j;
   }
-  float2 acc = make_float2(sr, si);
+  if (!colok) return;
+  const int jsafe = __ffs(colok) - 1;
+  float ar = sr, ai = si, aw = sw;
 #pragma unroll 1
   for (int l = 0; l < KB; ++l) {
+    int ky = sgn * (ky0 + l);
+    if (ky < -g.H || ky >= g.H) continue;
+    ky += ky < 0 ? g.S : 0;
     const float dy = fy - (float)l;
     const float ry = fmaf(dy, dy, uz2);
-    if (ry > g.a2) continue;
-    int ky = sgn * (ky0 + l);
-    if (EDGE && (ky < -g.H || ky >= g.H)) continue;
-    ky += ky < 0 ? g.S : 0;
     const unsigned char *row = ibase + (ky * row_bytes + sgn * kx0 * ESZ);
 #pragma unroll
     for (int j = 0; j < KB; ++j) {
       const float dx = fx - (float)j;
       const float r2 = fmaf(dx, dx, ry);
-      const float x = fmaf(r2, two_inv_a2, -1.0f);
-      const float x2 = x * x;
-      float2 eo = c[NP - 1];
-#pragma unroll
-      for (int k = NP - 2; k >= 0; --k) eo = __ffma2_rn(eo, make_float2(x2, x2), c[k]);
-      const bool ok = EDGE ? ((colok >> j) & 1u) != 0 : true;
-      const float w = (r2 <= g.a2 && ok) ? fmaf(eo.y, x, eo.x) : 0.0f;
-      const int off = (EDGE && !ok ? jsafe : j) * step;
-      const float2 p = ld_px<F16>(row + off);
-      acc = __ffma2_rn(make_float2(w, w), p, acc);
-      sw += w;
+      const bool ok = ((colok >> j) & 1u) != 0;
+      const float pv = poly_eo(c, fmaf(r2, two_inv_a2, -1.0f));
+      const float w = (r2 <= g.a2 && ok) ? pv : 0.0f;
+      const float2 p = ld_px<F16>(row + (ok ? j : jsafe) * step);
+      ar = fmaf(w, p.x, ar);
+      ai = fmaf(w, p.y, ai);
+      aw += w;
     }
   }
-  sr = acc.x;
-  si = acc.y;
+  sr = ar;
+  si = ai;
+  sw = aw;
 }
 
 // Careful path: any box, exact fold predicate (when near the fold plane) and
@@ -236,7 +271,7 @@ __device__ __noinline__ void box_careful(const InsertArgs &args, const float2 *l
 }
 
 template <int BX, int BY, int ZC, int WMODE, int KB, int F16>
-__global__ void __launch_bounds__(BX * BY, 2)
+__global__ void __launch_bounds__(BX * BY, 512 / (BX * BY))
 gather_kernel(const InsertArgs args) {
   constexpr int NT = BX * BY;
   constexpr int WV = 32 * ZC;                   // voxels per warp footprint
@@ -360,11 +395,11 @@ gather_kernel(const InsertArgs args) {
     if (kind == 0 || (kind == 1 && WMODE == W_POLY)) {
       if (WMODE == W_POLY) {
         if (kind == 0)
-          box_fast_poly<KB, F16, false>(args, cpair, ibase, sgn, kx0, ky0, fx, fy, uz2,
-                                        2.0f * inv_a2, sr, si, sw);
+          box_poly_interior<KB, F16>(args, cpair, ibase, sgn, kx0, ky0, fx, fy, uz2,
+                                     2.0f * inv_a2, sr, si, sw);
         else
-          box_fast_poly<KB, F16, true>(args, cpair, ibase, sgn, kx0, ky0, fx, fy, uz2,
-                                       2.0f * inv_a2, sr, si, sw);
+          box_poly_edge<KB, F16>(args, cpair, ibase, sgn, kx0, ky0, fx, fy, uz2, 2.0f * inv_a2,
+                                 sr, si, sw);
       } else {
         box_fast<WMODE, KB, F16>(args, lut, ibase, sgn, kx0, ky0, fx, fy, uz2, inv_a2, sr, si, sw);
       }
