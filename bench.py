@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--seed", type=int, default=5)
     p.add_argument("--profile-config", type=int, default=None,
                    help="profiling mode: time only this configuration id (no tuning, no baselines)")
+    p.add_argument("--phases", action="store_true",
+                   help="profiling mode: also report the gather kernel's per-phase cycle counters")
     return p.parse_args()
 
 
@@ -463,6 +465,12 @@ def run_profile(args):
     ctx = L.fr_create(args.S, float(np.float32(1.9)), 15.0, 0, 10000)
     L.fr_set_options(ctx, tuning=0, forced_config=args.profile_config)
     ups = L.fr_count_updates(ctx, rot)
+    phases = None
+    if args.phases:
+        L.fr_set_options(ctx, debug=2)
+        L.fr_insert(ctx, img, rot)
+        phases = L.fr_debug_phase_counters(ctx)
+        L.fr_set_options(ctx, debug=0)
     for _ in range(args.warmup):
         L.fr_insert(ctx, img, rot)
     torch.cuda.synchronize()
@@ -475,7 +483,7 @@ def run_profile(args):
     ms = s.elapsed_time(e) / args.steps
     print(json.dumps({"config": L.fr_describe_config(args.profile_config), "S": args.S, "n": args.n,
                       "ms_per_launch": ms, "updates_per_launch": ups,
-                      "updates_per_s": ups / (ms * 1e-3)}), flush=True)
+                      "updates_per_s": ups / (ms * 1e-3), "phases": phases}), flush=True)
     L.fr_destroy(ctx)
     return 0
 

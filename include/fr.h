@@ -97,7 +97,8 @@ typedef struct fr_options {
     int steps_per_insert;/* tuning steps (sub-batches) one fr_insert may take, >= 1 (default 4) */
     int forced_config;   /* >= 0: always use this configuration id; -1 (default): tuner decides */
     uint64_t seed;       /* seed of the search order (default 1) */
-    int debug;           /* 1: synchronise after every launch and check the device error word */
+    int debug;           /* bit 0: synchronise after every launch and check the device error
+                            word; bit 1: collect gather phase counters */
     int reserved[8];
 } fr_options;
 
@@ -230,6 +231,14 @@ int fr_last_cuda_error(void);
  * kx, ky, |k| <= 4096), out (device int[m], 1 = folded).  Test hook for the
  * predicate the insertion kernels use. */
 int fr_debug_fold(const float *r, const int *k, int m, int *out, void *stream);
+
+/* Diagnostics of the gather kernel, collected while fr_options.debug has bit
+ * 1 set: SM clock cycles its warps spent culling, queueing, draining fast,
+ * edge and careful items and flushing, the item counts of each kind, the
+ * list images and the rounds of fast items (16 counters, in that order; see
+ * the library's phase enumeration).  Copies up to cap counters to out (host)
+ * and clears them.  Synchronises the device. */
+int fr_debug_phase_counters(fr_ctx *ctx, unsigned long long *out, int cap);
 
 /* Evaluate the device blob weight for m squared distances r2 (device float[m])
  * into out (device float[m]): mode 0 the table, mode 1 the Abramowitz & Stegun

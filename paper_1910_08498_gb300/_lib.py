@@ -108,6 +108,7 @@ def _lib():
             "fr_last_cuda_error": (i, []),
             "fr_debug_fold": (i, [vp, vp, i, vp, vp]),
             "fr_debug_blob": (i, [vp, vp, i, i, vp, vp]),
+            "fr_debug_phase_counters": (i, [vp, P(ctypes.c_ulonglong), i]),
             "fr_mlp_num_params": (i, []),
             "fr_mlp_forward": (i, [vp, vp, i, vp, vp]),
             "fr_mlp_backward": (i, [vp, vp, vp, i, vp, vp, vp]),
@@ -309,6 +310,16 @@ def fr_debug_fold(r, k, out, stream=None):
 def fr_debug_blob(ctx, r2, mode, out, stream=None):
     return _check(_lib().fr_debug_blob(ctx, _ptr(r2), r2.numel(), int(mode), _ptr(out),
                                        _stream(stream)), "fr_debug_blob")
+
+
+PHASES = ["cull", "queue", "drain_fast", "drain_edge", "drain_careful", "flush", "items_fast",
+          "items_edge", "items_careful", "list_images", "warp_cycles", "rounds_fast"]
+
+
+def fr_debug_phase_counters(ctx) -> dict:
+    out = (ctypes.c_ulonglong * 16)()
+    _check(_lib().fr_debug_phase_counters(ctx, out, 16), "fr_debug_phase_counters")
+    return {name: int(out[k]) for k, name in enumerate(PHASES)}
 
 
 def fr_mlp_num_params() -> int:

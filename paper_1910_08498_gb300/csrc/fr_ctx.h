@@ -34,6 +34,7 @@ struct fr_ctx {
     int4 *dev = nullptr;
   };
   Units units[8];
+  unsigned long long *d_phase = nullptr;  // gather phase counters (debug bit 1)
   // cost model
   float *d_mlp = nullptr;
   bool mlp_trained = false;

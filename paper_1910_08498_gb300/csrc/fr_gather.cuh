@@ -338,12 +338,20 @@ gather_kernel(const InsertArgs args) {
   }
   for (int i = lane; i < 3 * WV; i += 32) s_acc[i] = 0.f;
   __syncwarp();
+  // optional phase counters (warp-uniform control, lane 0 keeps the clocks)
+  const bool prof = args.phase != nullptr;
+  unsigned long long ph[PH_COUNT];
+#pragma unroll
+  for (int k = 0; k < PH_COUNT; ++k) ph[k] = 0;
+  const long long t_start = prof ? clock64() : 0;
+  auto tick = [&]() -> long long { return prof ? clock64() : 0; };
 
   // fold the warp's shared partial sums into HBM (lane owns its column's voxels):
   // straight into the double-float accumulators when this CTA is the only one
   // writing its brick, else into the float4 scratch (merged after the launch)
   auto flush = [&]() {
     __syncwarp();
+    const long long tf = tick();
     if (col_in) {
 #pragma unroll
       for (int t = 0; t < ZC; ++t) {
@@ -374,6 +382,7 @@ gather_kernel(const InsertArgs args) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) s_acc[c * WV + lane * ZC + t] = 0.f;
     __syncwarp();
+    if (prof) ph[PH_FLUSH] += (unsigned long long)(clock64() - tf);
   };
 
   // one queued (image, voxel) item: form the box sums and add them to the
@@ -420,8 +429,15 @@ gather_kernel(const InsertArgs args) {
   // to the front of the queue
   auto drain = [&](unsigned *q, int &qlen, int kind, bool all) {
     __syncwarp();
+    const long long t0 = tick();
     const int nfull = all ? qlen : (qlen & ~31);
     for (int k = lane; k < nfull; k += 32) process(q[k], kind);
+    if (prof) {
+      __syncwarp();
+      ph[PH_DRAIN_FAST + kind] += (unsigned long long)(clock64() - t0);
+      ph[PH_ITEMS_FAST + kind] += (unsigned long long)nfull;
+      if (kind == 0) ph[PH_ROUNDS] += (unsigned long long)((nfull + 31) / 32);
+    }
     __syncwarp();
     const int rest = qlen - nfull;
     if (rest) {
@@ -512,6 +528,7 @@ gather_kernel(const InsertArgs args) {
   int nl = 0;           // entries in the warp's list
   int since_flush = 0;  // list entries queued since the last flush
   auto process_list = [&]() {
+    if (prof) ph[PH_LIST_IMAGES] += (unsigned long long)nl;
     for (int li = 0; li < nl; ++li) {
       enqueue(li);
       if (++since_flush >= GATHER_FLUSH) {
@@ -531,6 +548,7 @@ gather_kernel(const InsertArgs args) {
 
   // ---- cull: one image per lane; kept images go to the warp's list in order
   for (int cs = img0; cs < img1; cs += 32) {
+    const long long tc = tick();
     const int i = cs + lane;
     bool keep = false;
     float e1x = 0, e1y = 0, e1z = 0, e2x = 0, e2y = 0, e2z = 0, mx = 0, my = 0, mz = 0;
@@ -567,10 +585,21 @@ gather_kernel(const InsertArgs args) {
     }
     nl += __popc(bal);
     __syncwarp();
+    if (prof) ph[PH_CULL] += (unsigned long long)(clock64() - tc);
     if (nl > lcap - 32) process_list();
   }
   process_list();
   flush();
+  if (prof && lane == 0) {
+    ph[PH_WARP_CYCLES] = (unsigned long long)(clock64() - t_start);
+    // queueing time = total minus the other phases
+    unsigned long long other = ph[PH_CULL] + ph[PH_DRAIN_FAST] + ph[PH_DRAIN_EDGE] +
+                               ph[PH_DRAIN_CAREFUL] + ph[PH_FLUSH];
+    ph[PH_QUEUE] = ph[PH_WARP_CYCLES] > other ? ph[PH_WARP_CYCLES] - other : 0;
+#pragma unroll
+    for (int k = 0; k < PH_COUNT; ++k)
+      if (ph[k]) atomicAdd(args.phase + k, ph[k]);
+  }
 }
 
 }  // namespace fr

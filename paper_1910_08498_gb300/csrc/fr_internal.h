@@ -57,8 +57,18 @@ struct InsertArgs {
   const int4 *units;    // work units: (brick x, y, z, split | nsplit << 16), one per CTA
   int nunits;
   int any_split;        // 1 if some unit shares its brick with other units
+  unsigned long long *phase;  // optional per-phase cycle and item counters (PH_*), or null
   // scatter
   float4 *scratch;      // [z][y][x - xa0] (re, im, w, 0)
+};
+
+// Per-phase counters of the gather kernel (diagnostics, enabled by
+// fr_options.debug bit 1): SM clock cycles spent by warps in each phase and
+// item counts.
+enum PhaseCounter {
+  PH_CULL = 0, PH_QUEUE, PH_DRAIN_FAST, PH_DRAIN_EDGE, PH_DRAIN_CAREFUL, PH_FLUSH,
+  PH_ITEMS_FAST, PH_ITEMS_EDGE, PH_ITEMS_CAREFUL, PH_LIST_IMAGES, PH_WARP_CYCLES, PH_ROUNDS,
+  PH_COUNT = 16
 };
 
 // Error bits written to the device error word.

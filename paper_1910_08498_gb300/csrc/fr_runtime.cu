@@ -91,6 +91,7 @@ InsertArgs base_args(const fr_ctx *c) {
   for (int k = 0; k < POLY_N; ++k) a.poly[k] = c->poly[k];
   a.err = c->d_err;
   a.scratch = c->scratch;
+  a.phase = (c->opt.debug & 2) ? c->d_phase : nullptr;
   return a;
 }
 
@@ -372,6 +373,9 @@ int fr_create(int S, const fr_blob *blob, fr_ctx **out) {
   cudaMemset(c->d_err, 0, sizeof(int));
   e = cudaMalloc(&c->d_count, sizeof(unsigned long long));
   if (e != cudaSuccess) return fail(cuda_fail(e));
+  e = cudaMalloc(&c->d_phase, PH_COUNT * sizeof(unsigned long long));
+  if (e != cudaSuccess) return fail(cuda_fail(e));
+  cudaMemset(c->d_phase, 0, PH_COUNT * sizeof(unsigned long long));
 
   // blob table: b at r^2 = i a^2 / (N - 1), (value, next - value); I0 from the
   // C++17 special-function library in double precision
@@ -437,6 +441,7 @@ int fr_destroy(fr_ctx *c) {
   cudaFree(c->scratch);
   cudaFree(c->d_err);
   cudaFree(c->d_count);
+  cudaFree(c->d_phase);
   cudaFree(c->d_mlp);
   for (auto &u : c->units) cudaFree(u.dev);
   delete c;
@@ -605,6 +610,16 @@ int fr_last_device_error(fr_ctx *c) {
 }
 
 int fr_last_cuda_error(void) { return g_last_cuda.load(); }
+
+int fr_debug_phase_counters(fr_ctx *c, unsigned long long *out, int cap) {
+  if (!c || !out || cap < 0) return FR_ERR_INVALID_ARG;
+  FR_CUDA(cudaDeviceSynchronize());
+  unsigned long long h[PH_COUNT];
+  FR_CUDA(cudaMemcpy(h, c->d_phase, sizeof h, cudaMemcpyDeviceToHost));
+  FR_CUDA(cudaMemset(c->d_phase, 0, sizeof h));
+  for (int k = 0; k < cap && k < PH_COUNT; ++k) out[k] = h[k];
+  return FR_OK;
+}
 
 int fr_debug_fold(const float *r, const int *k, int m, int *out, void *stream) {
   if (m < 0 || (m > 0 && (!r || !k || !out))) return FR_ERR_INVALID_ARG;
