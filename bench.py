@@ -474,16 +474,20 @@ def run_profile(args):
     for _ in range(args.warmup):
         L.fr_insert(ctx, img, rot)
     torch.cuda.synchronize()
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s.record()
     for _ in range(args.steps):
         L.fr_insert(ctx, img, rot)
     e.record()
     torch.cuda.synchronize()
+    clocks = clk.stop()
     ms = s.elapsed_time(e) / args.steps
     print(json.dumps({"config": L.fr_describe_config(args.profile_config), "S": args.S, "n": args.n,
                       "ms_per_launch": ms, "updates_per_launch": ups,
-                      "updates_per_s": ups / (ms * 1e-3), "phases": phases}), flush=True)
+                      "updates_per_s": ups / (ms * 1e-3), "phases": phases,
+                      "clocks": clocks}), flush=True)
     L.fr_destroy(ctx)
     return 0
 

@@ -176,7 +176,7 @@ __device__ __forceinline__ float blob_otf(float r2, float inv_a2, float alpha, f
 }
 
 // Polynomial blob: b(r) = sum_k c_k x^k, x = 2 r^2 / a^2 - 1, the
-// Chebyshev interpolant of degree 13 converted to the power basis on the host,
+// Chebyshev interpolant of degree 11 converted to the power basis on the host,
 // evaluated as E(x^2) + x O(x^2) with E, O the even and odd parts (Horner in
 // x^2 for each; absolute error below 1e-6 for the blobs it is enabled for).
 // The branch-free gather box runs the same operations with packed FMAs.

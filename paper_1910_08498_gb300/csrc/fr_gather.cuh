@@ -217,6 +217,64 @@ __device__ __forceinline__ void box_poly_edge(const InsertArgs &args, const floa
   sw = aw;
 }
 
+// Box crossing the column kx = 0, for a voxel with x > floor(a).  Every point
+// R c of the extended plane within a of such a voxel has (R c)_x > 0, so no
+// fold test is needed: a column c_x > 0 reads the stored pixel c, a column
+// c_x < 0 reads the stored -c conjugated, and the column c_x = 0 reads both
+// (0, c_y) and, conjugated, (0, -c_y) -- the rfft column kx = 0 holds both
+// halves, and the stored one of each pair that lands at -R c is folded onto
+// R c.  Branch free: pixels outside the image get weight 0 and read pixel 0.
+template <int KB, int F16>
+__device__ __forceinline__ void box_poly_straddle(const InsertArgs &args, const float2 *c,
+                                                  const unsigned char *ibase, int kx0, int ky0,
+                                                  float fx, float fy, float uz2,
+                                                  float two_inv_a2, float &sr, float &si,
+                                                  float &sw) {
+  const Geom &g = args.g;
+  constexpr int ESZ = F16 ? 4 : 8;
+  const int row_bytes = g.NX * ESZ;
+  const int j0 = -kx0;  // box column of kx = 0, in [0, KB)
+  const float dx0 = fx - (float)j0;
+  float ar = 0.f, ai = 0.f, aw = 0.f;
+#pragma unroll 1
+  for (int l = 0; l < KB; ++l) {
+    const int cy = ky0 + l;
+    const bool dok = cy >= -g.H && cy < g.H;  // row of the direct pixel (., cy) is stored
+    const bool mok = cy > -g.H && cy <= g.H;  // row of the mirrored pixel (., -cy) is stored
+    const int drow = dok ? (cy < 0 ? cy + g.S : cy) : 0;
+    const int mrow = mok ? (cy > 0 ? g.S - cy : -cy) : 0;
+    const float dy = fy - (float)l;
+    const float ry = fmaf(dy, dy, uz2);
+#pragma unroll
+    for (int j = 0; j < KB; ++j) {
+      const int cx = kx0 + j;
+      const bool neg = cx < 0;
+      const int pc = neg ? -cx : cx;
+      const bool ok = pc <= g.H && (neg ? mok : dok);
+      const float dx = fx - (float)j;
+      const float r2 = fmaf(dx, dx, ry);
+      const float pv = poly_eo(c, fmaf(r2, two_inv_a2, -1.0f));
+      const float w = (r2 <= g.a2 && ok) ? pv : 0.0f;
+      const int off = ok ? ((neg ? mrow : drow) * row_bytes + pc * ESZ) : 0;
+      const float2 p = ld_px<F16>(ibase + off);
+      ar = fmaf(w, p.x, ar);
+      ai = fmaf(neg ? -w : w, p.y, ai);
+      aw += w;
+    }
+    // column kx = 0, second half: stored (0, -cy), conjugated
+    const float r2 = fmaf(dx0, dx0, ry);
+    const float pv = poly_eo(c, fmaf(r2, two_inv_a2, -1.0f));
+    const float w = (r2 <= g.a2 && mok) ? pv : 0.0f;
+    const float2 p = ld_px<F16>(ibase + mrow * row_bytes);
+    ar = fmaf(w, p.x, ar);
+    ai = fmaf(-w, p.y, ai);
+    aw += w;
+  }
+  sr = ar;
+  si = ai;
+  sw = aw;
+}
+
 // Careful path: any box, exact fold predicate (when near the fold plane) and
 // range tests per pixel; the W weight counts each contribution.
 template <int WMODE, int KB, int F16>
@@ -414,10 +472,16 @@ gather_kernel(const InsertArgs args) {
       }
       si *= (float)sgn;
     } else {
-      const float e[6] = {LF(LF_E1X, li), LF(LF_E1Y, li), LF(LF_E1Z, li),
-                          LF(LF_E2X, li), LF(LF_E2Y, li), LF(LF_E2Z, li)};
-      box_careful<WMODE, KB, F16>(args, lut, ibase, e, kx0, ky0, fx, fy, uz2, sx <= -g.xa0, sx,
-                                  sy, sz, inv_a2, sr, si, sw);
+      if (WMODE == W_POLY && sx > -g.xa0) {
+        // a box crossing kx = 0 for a voxel away from the fold plane
+        box_poly_straddle<KB, F16>(args, cpair, ibase, kx0, ky0, fx, fy, uz2, 2.0f * inv_a2, sr,
+                                   si, sw);
+      } else {
+        const float e[6] = {LF(LF_E1X, li), LF(LF_E1Y, li), LF(LF_E1Z, li),
+                            LF(LF_E2X, li), LF(LF_E2Y, li), LF(LF_E2Z, li)};
+        box_careful<WMODE, KB, F16>(args, lut, ibase, e, kx0, ky0, fx, fy, uz2, sx <= -g.xa0, sx,
+                                    sy, sz, inv_a2, sr, si, sw);
+      }
     }
     const int slot = src * ZC + t;
     atomicAdd(&s_acc[slot], sr);

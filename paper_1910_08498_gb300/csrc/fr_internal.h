@@ -19,7 +19,7 @@ namespace fr {
 // Stegun Bessel approximations evaluated per pixel, or a Chebyshev polynomial
 // in r^2 held in registers (both on the fly)
 enum WeightMode { W_LUT = 0, W_OTF = 1, W_POLY = 2 };
-constexpr int POLY_N = 14;  // coefficients of the degree-13 weight polynomial
+constexpr int POLY_N = 12;  // coefficients of the degree-11 weight polynomial
 enum Algo { ALGO_GATHER = 0, ALGO_SCATTER = 1 };
 
 struct Geom {
