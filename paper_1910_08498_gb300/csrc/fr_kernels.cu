@@ -263,11 +263,14 @@ static cudaError_t launch_scatter_t(int threads, const InsertArgs &a, cudaStream
 
 cudaError_t launch_scatter(int threads, int wmode, const InsertArgs &a, cudaStream_t st,
                            int query_only, KernelInfo *info) {
-  if (a.g.KB == 4)
-    return wmode == W_LUT ? launch_scatter_t<W_LUT, 4>(threads, a, st, query_only, info)
-                          : launch_scatter_t<W_OTF, 4>(threads, a, st, query_only, info);
-  return wmode == W_LUT ? launch_scatter_t<W_LUT, 6>(threads, a, st, query_only, info)
-                        : launch_scatter_t<W_OTF, 6>(threads, a, st, query_only, info);
+  if (a.g.KB == 4) {
+    if (wmode == W_LUT) return launch_scatter_t<W_LUT, 4>(threads, a, st, query_only, info);
+    if (wmode == W_POLY) return launch_scatter_t<W_POLY, 4>(threads, a, st, query_only, info);
+    return launch_scatter_t<W_OTF, 4>(threads, a, st, query_only, info);
+  }
+  if (wmode == W_LUT) return launch_scatter_t<W_LUT, 6>(threads, a, st, query_only, info);
+  if (wmode == W_POLY) return launch_scatter_t<W_POLY, 6>(threads, a, st, query_only, info);
+  return launch_scatter_t<W_OTF, 6>(threads, a, st, query_only, info);
 }
 
 cudaError_t launch_merge_scratch(const InsertArgs &a, cudaStream_t st) {
