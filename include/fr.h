@@ -60,7 +60,8 @@ typedef enum fr_status {
     FR_ERR_DEVICE_ASSERT = 6, /* a device-side range check fired (results invalid) */
     FR_ERR_TIMEOUT = 7,       /* a bounded device wait gave up (results invalid) */
     FR_ERR_IO = 8,            /* a tuning file could not be read or written */
-    FR_ERR_STATE = 9          /* the call is not valid in the context's current state */
+    FR_ERR_STATE = 9,         /* the call is not valid in the context's current state */
+    FR_ERR_NOALLOC_LIMIT = 10 /* the size exceeds the fixed scratch of fr_insert_noalloc */
 } fr_status;
 
 typedef enum fr_dtype { FR_F32 = 0, FR_F16 = 1 } fr_dtype;

@@ -19,6 +19,8 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "fr.h")
 
 FR_OK, FR_ERR_INVALID_ARG, FR_ERR_UNSUPPORTED, FR_ERR_OOM, FR_ERR_CUDA = 0, 1, 2, 3, 4
 FR_ERR_LAUNCH, FR_ERR_DEVICE_ASSERT, FR_ERR_TIMEOUT, FR_ERR_IO, FR_ERR_STATE = 5, 6, 7, 8, 9
+FR_ERR_NOALLOC_LIMIT = 10
+FR_NOALLOC_MAX_S = 64
 FR_F32, FR_F16 = 0, 1
 FR_SEARCH_EXHAUSTIVE, FR_SEARCH_RANDOM, FR_SEARCH_LEARNED = 0, 1, 2
 MLP_NPARAM = 5313
@@ -63,11 +65,15 @@ _LIB = None
 _LOCK = threading.Lock()
 
 
-def declared_symbols(header: str = HEADER) -> list[str]:
-    """Names of the functions include/fr.h declares."""
-    txt = open(header).read()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(fr_[a-z0-9_]+)\s*\(", txt)))
+def declared_symbols(header: str | None = None) -> list[str]:
+    """Names of the functions one header (default: every include/*.h) declares."""
+    import glob
+    paths = [header] if header else sorted(glob.glob(os.path.join(os.path.dirname(HEADER), "*.h")))
+    names = set()
+    for path in paths:
+        txt = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
+        names.update(re.findall(r"\b(fr_[a-z0-9_]+)\s*\(", txt))
+    return sorted(names)
 
 
 def _lib():
@@ -116,6 +122,7 @@ def _lib():
             "fr_mlp_train": (i, [vp, P(f), P(f), i, i, f, ctypes.c_uint64, P(f)]),
             "fr_mlp_get": (i, [vp, P(f)]),
             "fr_mlp_set": (i, [vp, P(f)]),
+            "fr_insert_noalloc": (i, [i, f, f, vp, i, vp, i, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -185,6 +192,18 @@ def fr_insert(ctx, images, rotations, n: int | None = None, stream=None, allow_f
     ok = (FR_OK, FR_ERR_LAUNCH) if allow_fallback else (FR_OK,)
     return _check(_lib().fr_insert(ctx, _ptr(images), _dtype_of(images), _ptr(rotations), int(n),
                                    _stream(stream)), "fr_insert", ok)
+
+
+def fr_insert_noalloc(S, images, rotations, V, W, a=1.9, alpha=15.0, n=None, stream=None):
+    """Insertion with no device allocation (S <= FR_NOALLOC_MAX_S): adds the
+    batch to caller-owned V (complex64, (S+1)^3) and W (float32, (S+1)^3)."""
+    if n is None:
+        n = rotations.shape[0]
+    for t in (images, rotations, V, W):
+        assert t.is_cuda and t.is_contiguous()
+    return _check(_lib().fr_insert_noalloc(int(S), float(a), float(alpha), _ptr(images),
+                                           _dtype_of(images), _ptr(rotations), int(n), _ptr(V),
+                                           _ptr(W), _stream(stream)), "fr_insert_noalloc")
 
 
 def fr_insert_batched(ctxs, images, rotations, ns=None, capture=0, stream=None):

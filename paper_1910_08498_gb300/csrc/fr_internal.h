@@ -91,6 +91,10 @@ cudaError_t launch_gather(int shape_id, int wmode, const InsertArgs &a, cudaStre
 cudaError_t launch_scatter(int threads, int wmode, const InsertArgs &a, cudaStream_t st,
                            int query_only, KernelInfo *info);
 cudaError_t launch_merge_scratch(const InsertArgs &a, cudaStream_t st);
+// 1 / (A&S 9.8.2 polynomial at 3.75 / alpha): the constant of the on-the-fly weights
+float otf_inv_pa(double alpha);
+// record a CUDA error for fr_last_cuda_error
+void fr_note_cuda_error(int e);
 cudaError_t launch_finalize(const Geom &g, const float *acc, size_t plane, float2 *V, float *W,
                             cudaStream_t st);
 cudaError_t launch_count(const Geom &g, const float *rot, int n, unsigned long long *out,

@@ -95,6 +95,12 @@ InsertArgs base_args(const fr_ctx *c) {
   return a;
 }
 
+void fr_note_cuda_error(int e) { g_last_cuda.store(e); }
+
+float otf_inv_pa(double alpha) {
+  return alpha > 3.75 ? (float)(1.0 / as_982_host(3.75 / alpha)) : 1.0f;
+}
+
 static int ensure_scratch(fr_ctx *c) {
   if (c->scratch) return FR_OK;
   FR_CUDA(cudaMalloc(&c->scratch, c->plane * sizeof(float4)));
@@ -594,6 +600,8 @@ const char *fr_error_string(int s) {
     case FR_ERR_TIMEOUT: return "device wait timed out";
     case FR_ERR_IO: return "tuning file I/O error";
     case FR_ERR_STATE: return "invalid state";
+    case FR_ERR_NOALLOC_LIMIT:
+      return "size exceeds the fixed scratch of fr_insert_noalloc (S <= 64)";
     default: return "unknown status";
   }
 }
