@@ -150,13 +150,21 @@ int fr_insert(fr_ctx *ctx, const void *images, fr_dtype dtype, const float *rota
               int n, void *stream);
 
 /* Insert nb batches, batch b into context ctxs[b] (contexts may differ in S
- * and blob and may repeat), in one persistent kernel launch fed by a device
- * work queue; with capture = 1 the launch sequence (descriptor upload +
- * kernel + merges) is captured into a CUDA graph that later calls with the
- * same shapes replay.  All arrays are host arrays of nb entries; images[b]
- * and rotations[b] are device pointers.  Each context's tile shape is the
- * one its tuner picked (or its default).  Same semantics per batch as
- * fr_insert. */
+ * and blob and may repeat).  All arrays are host arrays of nb entries;
+ * images[b] and rotations[b] are device pointers.  Each batch runs the gather
+ * configuration its context's tuner picked for its key (or the default; a
+ * scatter choice is replaced by the default gather).  Batches that share
+ * brick shape, candidate-box width, image dtype and list capacity run in ONE
+ * persistent kernel launch: each warp takes (work unit, footprint) items from
+ * a device counter, heaviest units first, so uneven S and n share the GPU
+ * without a tail per batch.  A context that appears more than once receives
+ * its sums through its scratch volume with atomics.  The first call with a
+ * given (contexts, pointers, sizes, dtypes, configurations) builds a plan and
+ * uploads it (synchronously); later calls reuse it.  With capture = 1 the
+ * plan's launch sequence (counter reset, persistent kernels, scratch merges)
+ * is captured, on a stream the library owns, into a CUDA graph at the first
+ * call; that call and later ones launch the graph on `stream`.  Same semantics per batch as fr_insert (every image exactly once);
+ * no tuning steps are taken here. */
 int fr_insert_batched(fr_ctx *const *ctxs, const void *const *images, const fr_dtype *dtypes,
                       const float *const *rotations, const int *n, int nb, int capture,
                       void *stream);

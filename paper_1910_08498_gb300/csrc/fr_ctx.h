@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "../../include/fr.h"
 #include "fr_internal.h"
 #include "fr_tuner.h"
@@ -44,6 +46,17 @@ struct fr_ctx {
 namespace fr {
 int key_bucket(int n);
 InsertArgs base_args(const fr_ctx *c);
+// allocate the context's float4 scratch volume if it has none yet
+int ensure_scratch(fr_ctx *c);
+// gather work unit with its expected load (images it scans)
+struct UnitLoad {
+  double load;
+  int4 unit;  // brick x, y, z; split | nsplit << 16
+};
+double gather_unit_loads(const fr_ctx *c, int shape, int n, double target,
+                         std::vector<UnitLoad> &out, int &any_split);
+// drop cached batched-insertion plans that refer to c (called by fr_destroy)
+void batched_forget(const fr_ctx *c);
 int do_insert_ctx(fr_ctx *c, const void *images, fr_dtype dtype, const float *rot, int n,
                   cudaStream_t st);
 }  // namespace fr

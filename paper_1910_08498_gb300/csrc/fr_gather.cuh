@@ -328,39 +328,46 @@ __device__ __noinline__ void box_careful(const InsertArgs &args, const float2 *l
   }
 }
 
+// Per-warp shared memory of the gather: image list, partial sums, item queues.
+__host__ __device__ constexpr size_t gather_warp_smem(int zc, int chunk) {
+  return (size_t)LIST_FIELDS * chunk * 4 + (size_t)3 * (32 * zc) * 4 + (size_t)3 * (32 * zc + 32) * 4;
+}
+
+// Bytes of the InsertArgs copy at the head of each warp's shared memory in
+// the persistent gather.
+constexpr size_t GATHER_ARGS_BYTES = (sizeof(InsertArgs) + 15) & ~(size_t)15;
+
+// One warp's share of one work unit: the 8 x 4 x ZC footprint `warp` of the
+// brick (unit.x, unit.y, unit.z), over the images of the unit's split.
+// unit.w = split | nsplit << 16 | scratch << 30; partial sums go to the
+// double-float accumulators when the unit is the only writer of its brick
+// (nsplit == 1, no scratch flag), else to the float4 scratch with atomics.
+// wsmem is the warp's gather_warp_smem(args.chunk) bytes; lut the shared blob
+// table (W_LUT only).  No CTA-wide barrier is taken.
 template <int BX, int BY, int ZC, int WMODE, int KB, int F16>
-__global__ void __launch_bounds__(BX * BY, 512 / (BX * BY))
-gather_kernel(const InsertArgs args) {
-  constexpr int NT = BX * BY;
+__device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2 *lut,
+                                            unsigned char *wsmem, const int4 unit,
+                                            const int warp) {
   constexpr int WV = 32 * ZC;                   // voxels per warp footprint
   constexpr int QCAP = WV + 32;                 // entries per queue
   constexpr int ESZ = F16 ? 4 : 8;
-  static_assert(BX % 8 == 0 && BY % 4 == 0 && NT % 32 == 0, "warp footprint is 8 x 4 columns");
+  static_assert(BX % 8 == 0 && BY % 4 == 0 && (BX * BY) % 32 == 0,
+                "warp footprint is 8 x 4 columns");
   static_assert(ZC <= 8, "item encoding holds 3 bits of z");
   const Geom &g = args.g;
-  const int tid = threadIdx.x;
-  const int lane = tid & 31, warp = tid >> 5;
+  const int lane = threadIdx.x & 31;
   const int lcap = args.chunk;  // list capacity per warp
 
-  extern __shared__ __align__(16) unsigned char smem[];
-  unsigned char *sp = smem;
-  float2 *s_lut = reinterpret_cast<float2 *>(sp);
-  if (WMODE == W_LUT) sp += ((size_t)args.lut_n * sizeof(float2) + 15) & ~(size_t)15;
-  const size_t per_warp = (size_t)LIST_FIELDS * lcap * 4 + (size_t)3 * WV * 4 + (size_t)3 * QCAP * 4;
-  sp += (size_t)warp * per_warp;
-  float *s_list = reinterpret_cast<float *>(sp);         // [LIST_FIELDS][lcap]
+  float *s_list = reinterpret_cast<float *>(wsmem);      // [LIST_FIELDS][lcap]
   float *s_acc = s_list + (size_t)LIST_FIELDS * lcap;   // [3][WV]
   unsigned *s_qf = reinterpret_cast<unsigned *>(s_acc + 3 * WV);  // fast items
   unsigned *s_qe = s_qf + QCAP;                                    // fast items at the image edge
   unsigned *s_qc = s_qe + QCAP;                                    // careful items
-  const float2 *lut = s_lut;
   auto LF = [&](int f, int i) -> float & { return s_list[f * lcap + i]; };
   auto LI = [&](int f, int i) -> int { return __float_as_int(s_list[f * lcap + i]); };
 
-  // this CTA's work unit (brick and share of the images), this warp's
-  // footprint (8 x 4 columns, ZC deep)
-  const int4 unit = args.units[blockIdx.x];
-  const int split = unit.w & 0xffff, nsplit = unit.w >> 16;
+  const int split = unit.w & 0xffff, nsplit = (unit.w >> 16) & 0x3fff;
+  const bool to_scratch = nsplit > 1 || ((unit.w >> 30) & 1);
   const int img0 = (int)((long long)args.n * split / nsplit);
   const int img1 = (int)((long long)args.n * (split + 1) / nsplit);
   const int wx = warp % (BX / 8), wy = warp / (BX / 8);
@@ -390,10 +397,6 @@ gather_kernel(const InsertArgs args) {
 #pragma unroll
   for (int k = 0; k < POLY_N / 2; ++k) cpair[k] = make_float2(args.poly[2 * k], args.poly[2 * k + 1]);
 
-  if (WMODE == W_LUT) {
-    for (int i = tid; i < args.lut_n; i += NT) s_lut[i] = args.lut[i];
-    __syncthreads();  // the only CTA-wide barrier: warps run independently from here
-  }
   for (int i = lane; i < 3 * WV; i += 32) s_acc[i] = 0.f;
   __syncwarp();
   // optional phase counters (warp-uniform control, lane 0 keeps the clocks)
@@ -420,7 +423,7 @@ gather_kernel(const InsertArgs args) {
         const float ar = s_acc[lane * ZC + t], ai = s_acc[WV + lane * ZC + t],
                     aw = s_acc[2 * WV + lane * ZC + t];
         if (aw != 0.f || ar != 0.f || ai != 0.f) {
-          if (nsplit == 1) {
+          if (!to_scratch) {
             const float add[3] = {ar, ai, aw};
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -663,6 +666,66 @@ gather_kernel(const InsertArgs args) {
 #pragma unroll
     for (int k = 0; k < PH_COUNT; ++k)
       if (ph[k]) atomicAdd(args.phase + k, ph[k]);
+  }
+}
+
+// One CTA per work unit (args.units[blockIdx.x]); the CTA shares the blob
+// table, its warps then run independently.
+template <int BX, int BY, int ZC, int WMODE, int KB, int F16>
+__global__ void __launch_bounds__(BX * BY, 512 / (BX * BY))
+gather_kernel(const InsertArgs args) {
+  constexpr int NT = BX * BY;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned char *sp = smem;
+  float2 *s_lut = reinterpret_cast<float2 *>(sp);
+  if (WMODE == W_LUT) {
+    sp += ((size_t)args.lut_n * sizeof(float2) + 15) & ~(size_t)15;
+    for (int i = tid; i < args.lut_n; i += NT) s_lut[i] = args.lut[i];
+    __syncthreads();  // the only CTA-wide barrier: warps run independently from here
+  }
+  gather_warp<BX, BY, ZC, WMODE, KB, F16>(args, s_lut, sp + (size_t)warp * gather_warp_smem(ZC, args.chunk),
+                                          args.units[blockIdx.x], warp);
+}
+
+// Persistent gather over the work items of several batches (A8): each warp
+// takes (unit, footprint) items from a device counter until none are left, so
+// batches of different S and n share one launch.  items[i] = {bx | by << 10 |
+// bz << 20, split word, batch, 0}; an item index k names items[k / NW],
+// footprint k % NW (NW warps per brick).  The batch's arguments are copied to
+// the warp's shared memory when the batch changes.  Weights on the fly
+// (polynomial or Bessel), so no CTA-wide table and no CTA-wide barrier; the
+// counter is only incremented, never waited on.
+template <int BX, int BY, int ZC, int WMODE, int KB, int F16>
+__global__ void __launch_bounds__(BX * BY, 512 / (BX * BY))
+gather_persistent_kernel(const InsertArgs *__restrict__ descs, const int4 *__restrict__ items,
+                         int nitems, int chunk, unsigned *counter) {
+  static_assert(WMODE != W_LUT, "the persistent gather evaluates weights on the fly");
+  constexpr int NW = BX * BY / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned char *wbase = smem + (size_t)warp * (GATHER_ARGS_BYTES + gather_warp_smem(ZC, chunk));
+  InsertArgs *s_args = reinterpret_cast<InsertArgs *>(wbase);
+  unsigned char *wsmem = wbase + GATHER_ARGS_BYTES;
+  const unsigned total = (unsigned)nitems * NW;
+  int cur = -1;
+  for (;;) {
+    unsigned k = 0;
+    if (lane == 0) k = atomicAdd(counter, 1u);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    if (k >= total) break;
+    const int4 it = items[k / NW];
+    if (it.z != cur) {
+      __syncwarp();
+      const int *src = reinterpret_cast<const int *>(descs + it.z);
+      int *dst = reinterpret_cast<int *>(s_args);
+      for (int i = lane; i < (int)(sizeof(InsertArgs) / 4); i += 32) dst[i] = src[i];
+      __syncwarp();
+      cur = it.z;
+    }
+    const int4 unit = make_int4(it.x & 1023, (it.x >> 10) & 1023, (it.x >> 20) & 1023, it.y);
+    gather_warp<BX, BY, ZC, WMODE, KB, F16>(*s_args, nullptr, wsmem, unit, (int)(k % NW));
+    __syncwarp();
   }
 }
 

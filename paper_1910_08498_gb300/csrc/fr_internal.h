@@ -108,6 +108,18 @@ int num_gather_shapes();
 GatherShape gather_shape(int id);
 // dynamic shared memory a gather launch needs
 size_t gather_smem_bytes(const GatherShape &sh, int wmode, int lut_n, int chunk);
+size_t gather_persistent_smem_bytes(const GatherShape &sh, int chunk);
+
+// One persistent gather launch over the work items of several batches.
+struct PersistentLaunch {
+  const InsertArgs *descs;  // device, one per batch
+  const int4 *items;        // device, {bx | by << 10 | bz << 20, split word, batch, 0}
+  int nitems;
+  int chunk;                // image-list capacity per warp, common to all batches
+  unsigned *counter;        // device, zero at launch
+};
+cudaError_t launch_gather_persistent(int shape_id, int kb, int f16, const PersistentLaunch &p,
+                                     cudaStream_t st);
 
 // MLP kernels
 cudaError_t mlp_forward(const float *params, const float *x, int m, float *y, cudaStream_t st);

@@ -101,7 +101,7 @@ float otf_inv_pa(double alpha) {
   return alpha > 3.75 ? (float)(1.0 / as_982_host(3.75 / alpha)) : 1.0f;
 }
 
-static int ensure_scratch(fr_ctx *c) {
+int ensure_scratch(fr_ctx *c) {
   if (c->scratch) return FR_OK;
   FR_CUDA(cudaMalloc(&c->scratch, c->plane * sizeof(float4)));
   FR_CUDA(cudaMemset(c->scratch, 0, c->plane * sizeof(float4)));
@@ -112,19 +112,12 @@ static int ensure_scratch(fr_ctx *c) {
 // crossed, within a + (brick radius) r, by a fraction min(1, (a + r) / d) of
 // uniformly oriented planes through the origin, so its expected image count is
 // n min(1, (a + r) / d).  Bricks whose count exceeds a target share are split
-// into several units, each taking a contiguous range of the images, and units
-// are ordered heaviest first so the largest ones start first.
-static int gather_units(fr_ctx *c, const Config &cfg, int n, InsertArgs &a) {
-  for (int k = 0; k < 8; ++k) {
-    fr_ctx::Units &u = c->units[k];
-    if (u.dev && u.shape == cfg.shape && u.n == n) {
-      a.units = u.dev;
-      a.nunits = u.count;
-      a.any_split = u.any_split;
-      return FR_OK;
-    }
-  }
-  const GatherShape sh = gather_shape(cfg.shape);
+// into several units, each taking a contiguous range of the images.  `target`
+// <= 0 selects the share of one launch of this batch alone (total load over
+// 32 units per SM).  Returns the units with their expected loads, unsorted.
+double gather_unit_loads(const fr_ctx *c, int shape, int n, double target,
+                         std::vector<UnitLoad> &out, int &any_split) {
+  const GatherShape sh = gather_shape(shape);
   const Geom &g = c->g;
   const int nbx = (g.NXa + sh.bx - 1) / sh.bx, nby = (g.D + sh.by - 1) / sh.by,
             nbz = (g.D + sh.zc - 1) / sh.zc;
@@ -145,13 +138,14 @@ static int gather_units(fr_ctx *c, const Config &cfg, int n, InsertArgs &a) {
         load[((size_t)bz * nby + by) * nbx + bx] = l;
         total += l;
       }
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  const double target = std::max(64.0, total / (std::max(sms, 1) * 32.0));
-  struct U { double w; int4 v; };
-  std::vector<U> us;
-  us.reserve(load.size() + 64);
-  int any_split = 0;
+  if (target <= 0) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    target = std::max(64.0, total / (std::max(sms, 1) * 32.0));
+  }
+  out.clear();
+  out.reserve(load.size() + 64);
+  any_split = 0;
   for (int bz = 0; bz < nbz; ++bz)
     for (int by = 0; by < nby; ++by)
       for (int bx = 0; bx < nbx; ++bx) {
@@ -159,11 +153,31 @@ static int gather_units(fr_ctx *c, const Config &cfg, int n, InsertArgs &a) {
         int ns = (int)std::ceil(l / target);
         ns = std::max(1, std::min(ns, std::min(64, std::max(1, n / 32))));
         if (ns > 1) any_split = 1;
-        for (int s = 0; s < ns; ++s) us.push_back(U{l / ns, make_int4(bx, by, bz, s | (ns << 16))});
+        for (int s = 0; s < ns; ++s)
+          out.push_back(UnitLoad{l / ns, make_int4(bx, by, bz, s | (ns << 16))});
       }
-  std::stable_sort(us.begin(), us.end(), [](const U &p, const U &q) { return p.w > q.w; });
+  return total;
+}
+
+// Work units of a gather launch of this batch alone, heaviest first (so the
+// largest ones start first), cached on the device per (shape, n).
+static int gather_units(fr_ctx *c, const Config &cfg, int n, InsertArgs &a) {
+  for (int k = 0; k < 8; ++k) {
+    fr_ctx::Units &u = c->units[k];
+    if (u.dev && u.shape == cfg.shape && u.n == n) {
+      a.units = u.dev;
+      a.nunits = u.count;
+      a.any_split = u.any_split;
+      return FR_OK;
+    }
+  }
+  std::vector<UnitLoad> us;
+  int any_split = 0;
+  gather_unit_loads(c, cfg.shape, n, 0.0, us, any_split);
+  std::stable_sort(us.begin(), us.end(),
+                   [](const UnitLoad &p, const UnitLoad &q) { return p.load > q.load; });
   std::vector<int4> host(us.size());
-  for (size_t i = 0; i < us.size(); ++i) host[i] = us[i].v;
+  for (size_t i = 0; i < us.size(); ++i) host[i] = us[i].unit;
   // replace the oldest cached list
   fr_ctx::Units &slot = c->units[7];
   cudaFree(slot.dev);
@@ -441,6 +455,7 @@ int fr_create(int S, const fr_blob *blob, fr_ctx **out) {
 int fr_destroy(fr_ctx *c) {
   if (!c) return FR_OK;
   cudaDeviceSynchronize();
+  batched_forget(c);
   c->tuner.release();
   cudaFree(c->acc);
   cudaFree(c->lut);

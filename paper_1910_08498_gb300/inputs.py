@@ -99,3 +99,22 @@ CONFIG_SMALL = dict(S=32, n=64, seed=1, a=1.9, alpha=15.0, table=10000)
 CONFIG_TUNING = dict(S=128, batches=10, n=1000, seed=2, a=1.9, alpha=15.0)
 CONFIG_UNEVEN = dict(batches=40, S_choices=(64, 96, 128, 192, 256), n_range=(500, 5000), seed=3)
 CONFIG_LARGE = dict(S=256, n_total=100_000, n=5000, seed=5, a=1.9, alpha=15.0, S_switch=192)
+
+
+def uneven_batches(cfg=CONFIG_UNEVEN, batches=None):
+    """(S, n, seed) of each batch of the uneven-batch workload: S uniform over
+    cfg["S_choices"], n uniform over cfg["n_range"] (inclusive), drawn from a
+    CPU torch generator seeded with cfg["seed"]; batch b's images use seed
+    cfg["seed"] * 1000 + b."""
+    gen = torch.Generator()
+    gen.manual_seed(int(cfg["seed"]))
+    nb = cfg["batches"] if batches is None else batches
+    choices = cfg["S_choices"]
+    lo, hi = cfg["n_range"]
+    out = []
+    for b in range(nb):
+        S = int(choices[int(torch.randint(len(choices), (1,), generator=gen))])
+        n = int(torch.randint(lo, hi + 1, (1,), generator=gen))
+        out.append((S, n, int(cfg["seed"]) * 1000 + b))
+    return out
+
