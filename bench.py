@@ -17,7 +17,10 @@ Phases (one JSON line at the end):
   tuned    the configuration the tuner chose -- the headline `value`;
   e2e      the tuned path with host-resident (pinned) inputs copied in every
            step, the device status word read back every step, and the final
-           volume downloaded once at the end of the timed region.
+           volume downloaded once at the end of the timed region;
+  batched  the uneven-batch workload (40 batches of S in {64..256}, n in
+           [500, 5000]): one persistent-gather graph replay per pass against
+           one fr_insert per batch.
 
 --impl reference times the FP64 CPU oracle (the definition, written as a
 plain scatter) on the host cores on a bounded sample of the same workload.
@@ -55,6 +58,9 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target oracle work for cpu_baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-batched", action="store_true", help="skip the uneven-batch workload")
+    p.add_argument("--only-batched", action="store_true",
+                   help="profiling mode: run only the uneven-batch workload and print its result")
     p.add_argument("--seed", type=int, default=5)
     p.add_argument("--profile-config", type=int, default=None,
                    help="profiling mode: time only this configuration id (no tuning, no baselines)")
@@ -393,6 +399,10 @@ def run_ours(args):
             "peak_note": f"FP32 FMA peak: {sms} SMs x 128 lanes x 2 flops x {max_mhz:.0f} MHz (max SM clock)",
             "avg_launch_ms": 1e3 * per_launch_s, "updates_per_launch": ups_per_launch}
 
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(L, inputs, dev, stream, max(2, args.steps // 3), 1, f16)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         img0, rot0 = batches[0]
@@ -420,6 +430,7 @@ def run_ours(args):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "batched": batched,
         "gpu_launches": args.steps * launches_per_insert(L, best, n),
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
         "wall_s_timed": wall,
@@ -431,6 +442,58 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def run_batched(L, inputs, dev, stream, steps, warmup, f16):
+    """The uneven-batch workload (40 batches, S uniform over {64, 96, 128, 192,
+    256}, n uniform over [500, 5000], one volume per batch): all batches in
+    persistent gather launches replayed from a CUDA graph, against one
+    fr_insert per batch (the same default configuration, untuned)."""
+    import torch
+    spec = inputs.uneven_batches()
+    data, ctx_p, ctx_s = [], [], []
+    ups = 0
+    for S, n, seed in spec:
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(seed)
+        rot = inputs.random_rotations(n, gen, dev).contiguous()
+        img = inputs.random_images(S, n, gen, dev)
+        img = inputs.to_half(img) if f16 else img.contiguous()
+        data.append((img, rot))
+        for lst in (ctx_p, ctx_s):
+            c = L.fr_create(S, 1.9, 15.0, 0, 10000)
+            L.fr_set_options(c, tuning=0, forced_config=-1)
+            lst.append(c)
+        ups += L.fr_count_updates(ctx_p[-1], rot)
+    imgs = [d[0] for d in data]
+    rots = [d[1] for d in data]
+
+    def persistent(k):
+        for _ in range(k):
+            L.fr_insert_batched(ctx_p, imgs, rots, capture=1)
+
+    def sequential(k):
+        for _ in range(k):
+            for c, (img, rot) in zip(ctx_s, data):
+                L.fr_insert(c, img, rot)
+
+    out = {}
+    for name, fn in (("persistent_graph", persistent), ("per_batch_inserts", sequential)):
+        fn(max(1, warmup))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / steps
+        out[name] = {"value": ups / t, "ms_per_pass": 1e3 * t}
+    for c in ctx_p + ctx_s:
+        L.fr_destroy(c)
+    sizes = sorted({S for S, _, _ in spec})
+    return {"workload": f"{len(spec)} batches, S in {sizes}, n in [500, 5000] (seeded), one volume each, "
+                        f"{'FP16' if f16 else 'FP32'} images",
+            "updates_per_pass": ups, "images_per_pass": sum(n for _, n, _ in spec), **out}
 
 
 def launches_per_insert(L, cfg, n):
@@ -496,6 +559,17 @@ def main():
     args = parse()
     if args.profile_config is not None:
         return run_profile(args)
+    if args.only_batched:
+        import torch
+
+        from paper_1910_08498_gb300 import _lib as L
+        from paper_1910_08498_gb300 import inputs
+        dev = torch.device("cuda", 0)
+        L.lib()
+        res = run_batched(L, inputs, dev, torch.cuda.current_stream(), args.steps, args.warmup,
+                          args.dtype == "f16")
+        print(json.dumps(res), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -155,9 +155,9 @@ int fr_insert(fr_ctx *ctx, const void *images, fr_dtype dtype, const float *rota
  * configuration its context's tuner picked for its key (or the default; a
  * scatter choice is replaced by the default gather).  Batches that share
  * brick shape, candidate-box width, image dtype and list capacity run in ONE
- * persistent kernel launch: each warp takes (work unit, footprint) items from
- * a device counter, heaviest units first, so uneven S and n share the GPU
- * without a tail per batch.  A context that appears more than once receives
+ * persistent kernel launch: each CTA takes work units (a brick and a share of
+ * a batch's images) from a device counter, heaviest units first, so uneven S
+ * and n share the GPU without a tail per batch.  A context that appears more than once receives
  * its sums through its scratch volume with atomics.  The first call with a
  * given (contexts, pointers, sizes, dtypes, configurations) builds a plan and
  * uploads it (synchronously); later calls reuse it.  With capture = 1 the

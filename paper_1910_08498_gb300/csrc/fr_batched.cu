@@ -8,7 +8,7 @@
 //     (brick shape, candidate-box width, image dtype, list capacity);
 //   * each group's work units (bricks and image splits, with expected loads)
 //     are pooled over its batches with one splitting target and ordered
-//     heaviest first; a warp-level item is (unit, footprint);
+//     heaviest first; a CTA of the persistent kernel takes one unit at a time;
 //   * the per-batch launch arguments and the items are uploaded once into a
 //     device buffer the plan owns;
 //   * a launch clears each group's counter, runs the group's persistent

@@ -688,44 +688,44 @@ gather_kernel(const InsertArgs args) {
                                           args.units[blockIdx.x], warp);
 }
 
-// Persistent gather over the work items of several batches (A8): each warp
-// takes (unit, footprint) items from a device counter until none are left, so
-// batches of different S and n share one launch.  items[i] = {bx | by << 10 |
-// bz << 20, split word, batch, 0}; an item index k names items[k / NW],
-// footprint k % NW (NW warps per brick).  The batch's arguments are copied to
-// the warp's shared memory when the batch changes.  Weights on the fly
-// (polynomial or Bessel), so no CTA-wide table and no CTA-wide barrier; the
-// counter is only incremented, never waited on.
+// Persistent gather over the work units of several batches (A8): each CTA
+// takes units from a device counter until none are left, so batches of
+// different S and n share one launch; the CTA's warps work on the footprints
+// of one unit at a time (neighbouring columns, the same images: pixels shared
+// in L1).  items[i] = {bx | by << 10 | bz << 20, split word, batch, 0}.  The
+// batch's arguments are copied to shared memory when the batch changes.
+// Weights on the fly (polynomial or Bessel).  The counter is only
+// incremented, never waited on; the CTA barriers are between units.
 template <int BX, int BY, int ZC, int WMODE, int KB, int F16>
 __global__ void __launch_bounds__(BX * BY, 512 / (BX * BY))
 gather_persistent_kernel(const InsertArgs *__restrict__ descs, const int4 *__restrict__ items,
                          int nitems, int chunk, unsigned *counter) {
   static_assert(WMODE != W_LUT, "the persistent gather evaluates weights on the fly");
-  constexpr int NW = BX * BY / 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NT = BX * BY;
+  const int tid = threadIdx.x, warp = tid >> 5;
   extern __shared__ __align__(16) unsigned char smem[];
-  unsigned char *wbase = smem + (size_t)warp * (GATHER_ARGS_BYTES + gather_warp_smem(ZC, chunk));
-  InsertArgs *s_args = reinterpret_cast<InsertArgs *>(wbase);
-  unsigned char *wsmem = wbase + GATHER_ARGS_BYTES;
-  const unsigned total = (unsigned)nitems * NW;
+  InsertArgs *s_args = reinterpret_cast<InsertArgs *>(smem);
+  __shared__ int4 s_item;
+  unsigned char *wsmem = smem + GATHER_ARGS_BYTES + (size_t)warp * gather_warp_smem(ZC, chunk);
   int cur = -1;
   for (;;) {
-    unsigned k = 0;
-    if (lane == 0) k = atomicAdd(counter, 1u);
-    k = __shfl_sync(0xffffffffu, k, 0);
-    if (k >= total) break;
-    const int4 it = items[k / NW];
+    if (tid == 0) {
+      const unsigned k = atomicAdd(counter, 1u);
+      s_item = k < (unsigned)nitems ? items[k] : make_int4(0, 0, -1, 0);
+    }
+    __syncthreads();
+    const int4 it = s_item;
+    if (it.z < 0) break;
     if (it.z != cur) {
-      __syncwarp();
       const int *src = reinterpret_cast<const int *>(descs + it.z);
       int *dst = reinterpret_cast<int *>(s_args);
-      for (int i = lane; i < (int)(sizeof(InsertArgs) / 4); i += 32) dst[i] = src[i];
-      __syncwarp();
+      for (int i = tid; i < (int)(sizeof(InsertArgs) / 4); i += NT) dst[i] = src[i];
       cur = it.z;
     }
+    __syncthreads();
     const int4 unit = make_int4(it.x & 1023, (it.x >> 10) & 1023, (it.x >> 20) & 1023, it.y);
-    gather_warp<BX, BY, ZC, WMODE, KB, F16>(*s_args, nullptr, wsmem, unit, (int)(k % NW));
-    __syncwarp();
+    gather_warp<BX, BY, ZC, WMODE, KB, F16>(*s_args, nullptr, wsmem, unit, warp);
+    __syncthreads();  // s_item and s_args are rewritten next
   }
 }
 

@@ -40,7 +40,7 @@ size_t gather_smem_bytes(const GatherShape &sh, int wmode, int lut_n, int chunk)
 
 size_t gather_persistent_smem_bytes(const GatherShape &sh, int chunk) {
   const int nw = sh.bx * sh.by / 32;
-  return (size_t)nw * (GATHER_ARGS_BYTES + gather_warp_smem(sh.zc, chunk));
+  return GATHER_ARGS_BYTES + (size_t)nw * gather_warp_smem(sh.zc, chunk);
 }
 
 cudaError_t launch_gather(int shape_id, int wmode, const InsertArgs &a, cudaStream_t st,

@@ -113,7 +113,7 @@ size_t gather_persistent_smem_bytes(const GatherShape &sh, int chunk);
 // One persistent gather launch over the work items of several batches.
 struct PersistentLaunch {
   const InsertArgs *descs;  // device, one per batch
-  const int4 *items;        // device, {bx | by << 10 | bz << 20, split word, batch, 0}
+  const int4 *items;        // device, {bx | by << 10 | bz << 20, split word, batch, 0}, one per unit
   int nitems;
   int chunk;                // image-list capacity per warp, common to all batches
   unsigned *counter;        // device, zero at launch
