@@ -535,24 +535,41 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
     }
     if (!col_in) near = 0;
     if (!__any_sync(0xffffffffu, near != 0)) return;
-    // phase 2: classify only those
+    // Shortcut: every voxel of the footprint projects within rw of the
+    // centre's projection uc, so its box starts at kx0 in [uc_x - rw - a_box,
+    // uc_x + rw - a_box + 1).  If all boxes lie inside the stored half (or all
+    // inside the mirrored half) of the image, with a margin against rounding,
+    // and no column is a fold column, every near voxel is a fast item and the
+    // per-voxel classification is skipped.
     unsigned mf = 0, me = 0, mc = 0, mneg = 0;
-    for (unsigned m = near; m; m &= m - 1) {
-      const int t = __ffs(m) - 1;
-      const float dz = (float)(z0 + t) - cz;
-      const float uxr = fmaf(e1z, dz, bx), uyr = fmaf(e2z, dz, by);
-      const float ux = (float)cix + uxr, uy = (float)ciy + uyr;
-      if (fabsf(ux) <= reach && fabsf(uy) <= reach) {
-        const int kx0 = cix + (int)ceilf(uxr - a_box), ky0 = ciy + (int)ceilf(uyr - a_box);
-        const bool direct = kx0 >= 1, mirror = kx0 + KB - 1 <= -1;
-        if (!fold_col && (direct || mirror)) {
-          const bool interior = direct
-              ? (kx0 + KB - 1 <= g.H && ky0 >= -g.H && ky0 + KB - 1 < g.H)
-              : (kx0 >= -g.H && ky0 > -g.H && ky0 + KB - 1 <= g.H);
-          if (interior) mf |= 1u << t; else me |= 1u << t;
-          if (mirror) mneg |= 1u << t;
-        } else {
-          mc |= 1u << t;
+    const float ucx = (float)cix + LF(LF_FX, li), ucy = (float)ciy + LF(LF_FY, li);
+    const float xlo = ucx - rw - a_box - 0.01f, xhi = ucx + rw - a_box + (float)KB + 0.01f;
+    const float ylo = ucy - rw - a_box - 0.01f, yhi = ucy + rw - a_box + (float)KB + 0.01f;
+    const float Hf = (float)g.H;
+    const bool direct_all = xlo >= 1.f && xhi <= Hf && ylo >= -Hf && yhi <= Hf - 1.f;
+    const bool mirror_all = xhi <= -1.f && xlo >= -Hf && ylo > -Hf && yhi <= Hf;
+    if (fx0 > -g.xa0 && (direct_all || mirror_all)) {
+      mf = near;
+      mneg = mirror_all ? near : 0u;
+    } else {
+      // phase 2: classify the near voxels one by one
+      for (unsigned m = near; m; m &= m - 1) {
+        const int t = __ffs(m) - 1;
+        const float dz = (float)(z0 + t) - cz;
+        const float uxr = fmaf(e1z, dz, bx), uyr = fmaf(e2z, dz, by);
+        const float ux = (float)cix + uxr, uy = (float)ciy + uyr;
+        if (fabsf(ux) <= reach && fabsf(uy) <= reach) {
+          const int kx0 = cix + (int)ceilf(uxr - a_box), ky0 = ciy + (int)ceilf(uyr - a_box);
+          const bool direct = kx0 >= 1, mirror = kx0 + KB - 1 <= -1;
+          if (!fold_col && (direct || mirror)) {
+            const bool interior = direct
+                ? (kx0 + KB - 1 <= g.H && ky0 >= -g.H && ky0 + KB - 1 < g.H)
+                : (kx0 >= -g.H && ky0 > -g.H && ky0 + KB - 1 <= g.H);
+            if (interior) mf |= 1u << t; else me |= 1u << t;
+            if (mirror) mneg |= 1u << t;
+          } else {
+            mc |= 1u << t;
+          }
         }
       }
     }
@@ -586,76 +603,86 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
     qf += total & 1023;
     qe += (total >> 10) & 1023;
     qc += total >> 20;
-    if (qf >= 32) drain(s_qf, qf, 0, false);
-    if (qe >= 32) drain(s_qe, qe, 1, false);
-    if (qc >= 32) drain(s_qc, qc, 2, false);
+  };
+
+  // drain the queues that hold a full round (every queue entirely if `all`);
+  // the only place the boxes are evaluated, so each box's code exists once
+  auto service = [&](bool all) {
+    if (qf >= 32 || (all && qf > 0)) drain(s_qf, qf, 0, all);
+    if (qe >= 32 || (all && qe > 0)) drain(s_qe, qe, 1, all);
+    if (qc >= 32 || (all && qc > 0)) drain(s_qc, qc, 2, all);
   };
 
   const float *rot = args.rot;
   int nl = 0;           // entries in the warp's list
   int since_flush = 0;  // list entries queued since the last flush
-  auto process_list = [&]() {
-    if (prof) ph[PH_LIST_IMAGES] += (unsigned long long)nl;
-    for (int li = 0; li < nl; ++li) {
-      enqueue(li);
-      if (++since_flush >= GATHER_FLUSH) {
-        drain(s_qf, qf, 0, true);
-        drain(s_qe, qe, 1, true);
-        drain(s_qc, qc, 2, true);
-        flush();
-        since_flush = 0;
+  // Cull 32 images per step into the list; when the list is nearly full, or
+  // after the last image, queue and drain it.  Written as one loop with one
+  // site of each step so the code of every step exists once.
+  for (int cs = img0;; cs += 32) {
+    const bool last = cs >= img1;
+    if (!last) {
+      // ---- cull: one image per lane; kept images go to the warp's list in order
+      const long long tc = tick();
+      const int i = cs + lane;
+      bool keep = false;
+      float e1x = 0, e1y = 0, e1z = 0, e2x = 0, e2y = 0, e2z = 0, mx = 0, my = 0, mz = 0;
+      if (i < img1) {
+        const float *R = rot + 9 * (size_t)i;
+        e1x = __ldg(R + 0); e1y = __ldg(R + 3); e1z = __ldg(R + 6);
+        e2x = __ldg(R + 1); e2y = __ldg(R + 4); e2z = __ldg(R + 7);
+        mx = __ldg(R + 2);  my = __ldg(R + 5);  mz = __ldg(R + 8);
+        const float d = mx * cx + my * cy + mz * cz;
+        const float ux = e1x * cx + e1y * cy + e1z * cz;
+        const float uy = e2x * cx + e2y * cy + e2z * cz;
+        // the plane's distance to the footprint box is |d| minus its support
+        const float supp = fabsf(mx) * 3.5f + fabsf(my) * 1.5f + fabsf(mz) * hz;
+        keep = col_in_any(g, fx0, fy0) && fabsf(d) <= a + supp + 1e-3f && fabsf(ux) <= ext &&
+               fabsf(uy) <= ext;
       }
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      if (keep) {
+        const int o = nl + __popc(bal & ((1u << lane) - 1u));
+        float hx, lx, hy, ly, hz2, lz;
+        dot3_dd(e1x, e1y, e1z, cx, cy, cz, hx, lx);
+        dot3_dd(e2x, e2y, e2z, cx, cy, cz, hy, ly);
+        dot3_dd(mx, my, mz, cx, cy, cz, hz2, lz);
+        const float rx = rintf(hx), ry = rintf(hy);
+        LF(LF_E1X, o) = e1x; LF(LF_E1Y, o) = e1y; LF(LF_E1Z, o) = e1z;
+        LF(LF_E2X, o) = e2x; LF(LF_E2Y, o) = e2y; LF(LF_E2Z, o) = e2z;
+        LF(LF_MX, o) = mx;   LF(LF_MY, o) = my;   LF(LF_MZ, o) = mz;
+        LF(LF_FX, o) = (hx - rx) + lx;  // hx - rx is exact
+        LF(LF_FY, o) = (hy - ry) + ly;
+        LF(LF_UZ, o) = hz2 + lz;
+        LF(LF_CIX, o) = __int_as_float((int)rx);
+        LF(LF_CIY, o) = __int_as_float((int)ry);
+        LF(LF_IMG, o) = __int_as_float(i);
+      }
+      nl += __popc(bal);
+      __syncwarp();
+      if (prof) ph[PH_CULL] += (unsigned long long)(clock64() - tc);
     }
-    // the list is rebuilt next: nothing may refer to it afterwards
-    drain(s_qf, qf, 0, true);
-    drain(s_qe, qe, 1, true);
-    drain(s_qc, qc, 2, true);
-    nl = 0;
-  };
-
-  // ---- cull: one image per lane; kept images go to the warp's list in order
-  for (int cs = img0; cs < img1; cs += 32) {
-    const long long tc = tick();
-    const int i = cs + lane;
-    bool keep = false;
-    float e1x = 0, e1y = 0, e1z = 0, e2x = 0, e2y = 0, e2z = 0, mx = 0, my = 0, mz = 0;
-    if (i < img1) {
-      const float *R = rot + 9 * (size_t)i;
-      e1x = __ldg(R + 0); e1y = __ldg(R + 3); e1z = __ldg(R + 6);
-      e2x = __ldg(R + 1); e2y = __ldg(R + 4); e2z = __ldg(R + 7);
-      mx = __ldg(R + 2);  my = __ldg(R + 5);  mz = __ldg(R + 8);
-      const float d = mx * cx + my * cy + mz * cz;
-      const float ux = e1x * cx + e1y * cy + e1z * cz;
-      const float uy = e2x * cx + e2y * cy + e2z * cz;
-      // the plane's distance to the footprint box is |d| minus its support
-      const float supp = fabsf(mx) * 3.5f + fabsf(my) * 1.5f + fabsf(mz) * hz;
-      keep = col_in_any(g, fx0, fy0) && fabsf(d) <= a + supp + 1e-3f && fabsf(ux) <= ext &&
-             fabsf(uy) <= ext;
+    if (last || nl > lcap - 32) {
+      // ---- queue and accumulate the list's images; every GATHER_FLUSH
+      // images, drain everything and fold the partial sums into HBM
+      if (prof) ph[PH_LIST_IMAGES] += (unsigned long long)nl;
+      for (int li = 0; li <= nl; ++li) {
+        const bool end = li == nl;
+        bool all = end;  // the list is rebuilt next: nothing may refer to it afterwards
+        if (!end) {
+          enqueue(li);
+          if (++since_flush >= GATHER_FLUSH) all = true;
+        }
+        service(all);
+        if (all && since_flush >= GATHER_FLUSH) {
+          flush();
+          since_flush = 0;
+        }
+      }
+      nl = 0;
     }
-    const unsigned bal = __ballot_sync(0xffffffffu, keep);
-    if (keep) {
-      const int o = nl + __popc(bal & ((1u << lane) - 1u));
-      float hx, lx, hy, ly, hz2, lz;
-      dot3_dd(e1x, e1y, e1z, cx, cy, cz, hx, lx);
-      dot3_dd(e2x, e2y, e2z, cx, cy, cz, hy, ly);
-      dot3_dd(mx, my, mz, cx, cy, cz, hz2, lz);
-      const float rx = rintf(hx), ry = rintf(hy);
-      LF(LF_E1X, o) = e1x; LF(LF_E1Y, o) = e1y; LF(LF_E1Z, o) = e1z;
-      LF(LF_E2X, o) = e2x; LF(LF_E2Y, o) = e2y; LF(LF_E2Z, o) = e2z;
-      LF(LF_MX, o) = mx;   LF(LF_MY, o) = my;   LF(LF_MZ, o) = mz;
-      LF(LF_FX, o) = (hx - rx) + lx;  // hx - rx is exact
-      LF(LF_FY, o) = (hy - ry) + ly;
-      LF(LF_UZ, o) = hz2 + lz;
-      LF(LF_CIX, o) = __int_as_float((int)rx);
-      LF(LF_CIY, o) = __int_as_float((int)ry);
-      LF(LF_IMG, o) = __int_as_float(i);
-    }
-    nl += __popc(bal);
-    __syncwarp();
-    if (prof) ph[PH_CULL] += (unsigned long long)(clock64() - tc);
-    if (nl > lcap - 32) process_list();
+    if (last) break;
   }
-  process_list();
   flush();
   if (prof && lane == 0) {
     ph[PH_WARP_CYCLES] = (unsigned long long)(clock64() - t_start);
