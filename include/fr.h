@@ -242,11 +242,12 @@ int fr_last_cuda_error(void);
 int fr_debug_fold(const float *r, const int *k, int m, int *out, void *stream);
 
 /* Diagnostics of the gather kernel, collected while fr_options.debug has bit
- * 1 set: SM clock cycles its warps spent culling, queueing, draining fast,
- * edge and careful items and flushing, the item counts of each kind, the
- * list images and the rounds of fast items (16 counters, in that order; see
- * the library's phase enumeration).  Copies up to cap counters to out (host)
- * and clears them.  Synchronises the device. */
+ * 1 set (16 counters): 0 cull, 1 queue, 2-4 drain of fast, edge and kx = 0
+ * crossing items, 5 flush (SM clock cycles summed over warps); 6-8 item counts
+ * of those three kinds; 9 list images; 10 warp cycles in total; 11 rounds of
+ * fast items; 12 drain of fold-column items (cycles); 13 fold-column items.
+ * Copies up to cap counters to out (host) and clears them.  Synchronises the
+ * device. */
 int fr_debug_phase_counters(fr_ctx *ctx, unsigned long long *out, int cap);
 
 /* Evaluate the device blob weight for m squared distances r2 (device float[m])

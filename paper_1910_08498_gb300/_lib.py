@@ -332,7 +332,8 @@ def fr_debug_blob(ctx, r2, mode, out, stream=None):
 
 
 PHASES = ["cull", "queue", "drain_fast", "drain_edge", "drain_careful", "flush", "items_fast",
-          "items_edge", "items_careful", "list_images", "warp_cycles", "rounds_fast"]
+          "items_edge", "items_careful", "list_images", "warp_cycles", "rounds_fast", "drain_fold",
+          "items_fold"]
 
 
 def fr_debug_phase_counters(ctx) -> dict:

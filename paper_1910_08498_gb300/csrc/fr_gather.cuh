@@ -275,6 +275,96 @@ __device__ __forceinline__ void box_poly_straddle(const InsertArgs &args, const 
   sw = aw;
 }
 
+// Box of a voxel in a fold column (x <= floor(a)): the point R c of the
+// extended plane receives the stored pixel c when it is not folded (c_x >= 0,
+// R00 c_x + R01 c_y >= 0) and, conjugated, the stored pixel -c when that one is
+// folded (-c_x >= 0, R00 c_x + R01 c_y > 0) -- both for c_x = 0.  The signs are
+// exact (fold_pred).  Candidates whose FP32 r^2 is within rounding of a^2 are
+// left out of the branch-free pass and re-decided exactly afterwards (rare);
+// the DC pixel takes the exact |v|^2.
+template <int KB, int F16>
+__device__ __forceinline__ void box_poly_fold(const InsertArgs &args, const float2 *c,
+                                              const unsigned char *ibase, const float *e,
+                                              int kx0, int ky0, float fx, float fy, float uz2,
+                                              int vx, int vy, int vz, float two_inv_a2,
+                                              float &sr, float &si, float &sw) {
+  const Geom &g = args.g;
+  constexpr int ESZ = F16 ? 4 : 8;
+  const int row_bytes = g.NX * ESZ;
+  const float r00 = e[0], r01 = e[3];  // e = (e1x, e1y, e1z, e2x, e2y, e2z)
+  const float vr2 = (float)(vx * vx + vy * vy + vz * vz);
+  const float a2 = g.a2, tie_band = 1e-5f * g.a2;
+  const int j0 = -kx0;  // box column of kx = 0 (may lie outside [0, KB))
+  const bool has0 = j0 >= 0 && j0 < KB;
+  const float dx0 = fx - (float)j0;
+  unsigned long long ties = 0;
+  float ar = 0.f, ai = 0.f, aw = 0.f;
+  // contributions of box pixel (j, l) with weight w: the main pixel (c itself
+  // for c_x >= 0, -c for c_x < 0) and, in column kx = 0, the mirrored one
+  auto pixel = [&](int j, int l, float w) {
+    const int cx = kx0 + j, cy = ky0 + l;
+    const bool neg = cx < 0;
+    const int pc = neg ? -cx : cx, pr = neg ? -cy : cy;
+    const bool st = pc <= g.H && pr >= -g.H && pr < g.H;
+    const bool fo = st && fold_pred(r00, r01, pc, pr);
+    const bool ok = st && (neg ? fo : !fo);
+    const float wm = ok ? w : 0.f;
+    const float2 p = ld_px<F16>(ibase + (ok ? (pr < 0 ? pr + g.S : pr) * row_bytes + pc * ESZ : 0));
+    ar = fmaf(wm, p.x, ar);
+    ai = fmaf(neg ? -wm : wm, p.y, ai);
+    aw += wm;
+  };
+  auto column0 = [&](int l, float w) {
+    const int my = -(ky0 + l);
+    const bool st = my >= -g.H && my < g.H;
+    const bool ok = st && fold_pred(r00, r01, 0, my);
+    const float wm = ok ? w : 0.f;
+    const float2 p = ld_px<F16>(ibase + (ok ? (my < 0 ? my + g.S : my) * row_bytes : 0));
+    ar = fmaf(wm, p.x, ar);
+    ai = fmaf(-wm, p.y, ai);
+    aw += wm;
+  };
+#pragma unroll 1
+  for (int l = 0; l < KB; ++l) {
+    const int cy = ky0 + l;
+    const float dy = fy - (float)l;
+    const float ry = fmaf(dy, dy, uz2);
+#pragma unroll
+    for (int j = 0; j < KB; ++j) {
+      const int cx = kx0 + j;
+      const bool dc = cx == 0 && cy == 0;
+      const float dx = fx - (float)j;
+      const float r2 = dc ? vr2 : fmaf(dx, dx, ry);
+      const bool tie = !dc && fabsf(r2 - a2) <= tie_band;
+      ties |= (tie ? 1ull : 0ull) << (l * KB + j);
+      const float pv = poly_eo(c, fmaf(r2, two_inv_a2, -1.0f));
+      pixel(j, l, (r2 <= a2 && !tie) ? pv : 0.f);
+    }
+    // the kx = 0 column's second pixel (0, -cy)
+    const bool dc0 = cy == 0;
+    const float r2 = dc0 ? vr2 : fmaf(dx0, dx0, ry);
+    const bool tie0 = !dc0 && fabsf(r2 - a2) <= tie_band;
+    const float pv = poly_eo(c, fmaf(r2, two_inv_a2, -1.0f));
+    column0(l, (has0 && r2 <= a2 && !tie0) ? pv : 0.f);
+  }
+  // candidates within rounding of the blob edge: decide as the real numbers do
+  while (ties) {
+    const int b = __ffsll((long long)ties) - 1;
+    ties &= ties - 1;
+    const int l = b / KB, j = b - l * KB;
+    const int cx = kx0 + j, cy = ky0 + l;
+    if (!exact_r2_le_a2(vx, vy, vz, e[0], e[1], e[2], e[3], e[4], e[5], cx, cy, g.a)) continue;
+    const float dx = fx - (float)j, dy = fy - (float)l;
+    const float r2 = fminf(fmaf(dx, dx, fmaf(dy, dy, uz2)), a2);
+    const float w = poly_eo(c, fmaf(r2, two_inv_a2, -1.0f));
+    pixel(j, l, w);
+    if (cx == 0) column0(l, w);
+  }
+  sr = ar;
+  si = ai;
+  sw = aw;
+}
+
 // Careful path: any box, exact fold predicate (when near the fold plane) and
 // range tests per pixel; the W weight counts each contribution.
 template <int WMODE, int KB, int F16>
@@ -330,7 +420,7 @@ __device__ __noinline__ void box_careful(const InsertArgs &args, const float2 *l
 
 // Per-warp shared memory of the gather: image list, partial sums, item queues.
 __host__ __device__ constexpr size_t gather_warp_smem(int zc, int chunk) {
-  return (size_t)LIST_FIELDS * chunk * 4 + (size_t)3 * (32 * zc) * 4 + (size_t)3 * (32 * zc + 32) * 4;
+  return (size_t)LIST_FIELDS * chunk * 4 + (size_t)3 * (32 * zc) * 4 + (size_t)4 * (32 * zc + 32) * 4;
 }
 
 // Bytes of the InsertArgs copy at the head of each warp's shared memory in
@@ -362,7 +452,8 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
   float *s_acc = s_list + (size_t)LIST_FIELDS * lcap;   // [3][WV]
   unsigned *s_qf = reinterpret_cast<unsigned *>(s_acc + 3 * WV);  // fast items
   unsigned *s_qe = s_qf + QCAP;                                    // fast items at the image edge
-  unsigned *s_qc = s_qe + QCAP;                                    // careful items
+  unsigned *s_qc = s_qe + QCAP;                                    // boxes crossing kx = 0
+  unsigned *s_qd = s_qc + QCAP;                                    // voxels in fold columns
   auto LF = [&](int f, int i) -> float & { return s_list[f * lcap + i]; };
   auto LI = [&](int f, int i) -> int { return __float_as_int(s_list[f * lcap + i]); };
 
@@ -448,7 +539,8 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
 
   // one queued (image, voxel) item: form the box sums and add them to the
   // warp's partial sums
-  auto process = [&](unsigned it, int kind) {  // 0 fast, 1 fast at the image edge, 2 careful
+  // kinds: 0 fast, 1 fast at the image edge, 2 box crossing kx = 0, 3 fold column
+  auto process = [&](unsigned it, int kind) {
     const int li = (int)(it >> 9), src = (int)((it >> 3) & 31), t = (int)(it & 7);
     const int sgn = (it >> 8) & 1 ? -1 : 1;
     const int sx = fx0 + (src & 7), sy = fy0 + (src >> 3), sz = z0 + t;
@@ -474,17 +566,19 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
         box_fast<WMODE, KB, F16>(args, lut, ibase, sgn, kx0, ky0, fx, fy, uz2, inv_a2, sr, si, sw);
       }
       si *= (float)sgn;
+    } else if (kind == 2 && WMODE == W_POLY) {
+      // a box crossing kx = 0 for a voxel away from the fold plane
+      box_poly_straddle<KB, F16>(args, cpair, ibase, kx0, ky0, fx, fy, uz2, 2.0f * inv_a2, sr,
+                                 si, sw);
     } else {
-      if (WMODE == W_POLY && sx > -g.xa0) {
-        // a box crossing kx = 0 for a voxel away from the fold plane
-        box_poly_straddle<KB, F16>(args, cpair, ibase, kx0, ky0, fx, fy, uz2, 2.0f * inv_a2, sr,
-                                   si, sw);
-      } else {
-        const float e[6] = {LF(LF_E1X, li), LF(LF_E1Y, li), LF(LF_E1Z, li),
-                            LF(LF_E2X, li), LF(LF_E2Y, li), LF(LF_E2Z, li)};
-        box_careful<WMODE, KB, F16>(args, lut, ibase, e, kx0, ky0, fx, fy, uz2, sx <= -g.xa0, sx,
+      const float e[6] = {LF(LF_E1X, li), LF(LF_E1Y, li), LF(LF_E1Z, li),
+                          LF(LF_E2X, li), LF(LF_E2Y, li), LF(LF_E2Z, li)};
+      if (kind == 3 && WMODE == W_POLY)
+        box_poly_fold<KB, F16>(args, cpair, ibase, e, kx0, ky0, fx, fy, uz2, sx, sy, sz,
+                               2.0f * inv_a2, sr, si, sw);
+      else
+        box_careful<WMODE, KB, F16>(args, lut, ibase, e, kx0, ky0, fx, fy, uz2, kind == 3, sx,
                                     sy, sz, inv_a2, sr, si, sw);
-      }
     }
     const int slot = src * ZC + t;
     atomicAdd(&s_acc[slot], sr);
@@ -501,8 +595,8 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
     for (int k = lane; k < nfull; k += 32) process(q[k], kind);
     if (prof) {
       __syncwarp();
-      ph[PH_DRAIN_FAST + kind] += (unsigned long long)(clock64() - t0);
-      ph[PH_ITEMS_FAST + kind] += (unsigned long long)nfull;
+      ph[kind < 3 ? PH_DRAIN_FAST + kind : PH_DRAIN_FOLD] += (unsigned long long)(clock64() - t0);
+      ph[kind < 3 ? PH_ITEMS_FAST + kind : PH_ITEMS_FOLD] += (unsigned long long)nfull;
       if (kind == 0) ph[PH_ROUNDS] += (unsigned long long)((nfull + 31) / 32);
     }
     __syncwarp();
@@ -518,7 +612,7 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
 
   // queue the footprint's voxels near the plane of list entry li that the
   // extended plane reaches: fast, fast at the image edge, and careful apart
-  int qf = 0, qe = 0, qc = 0;
+  int qf = 0, qe = 0, qc = 0, qd = 0;
   auto enqueue = [&](int li) {
     const float mx = LF(LF_MX, li), my = LF(LF_MY, li), mz = LF(LF_MZ, li);
     const float bz = fmaf(my, dvy, fmaf(mx, dvx, LF(LF_UZ, li)));
@@ -541,7 +635,7 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
     // inside the mirrored half) of the image, with a margin against rounding,
     // and no column is a fold column, every near voxel is a fast item and the
     // per-voxel classification is skipped.
-    unsigned mf = 0, me = 0, mc = 0, mneg = 0;
+    unsigned mf = 0, me = 0, mc = 0, md = 0, mneg = 0;
     const float ucx = (float)cix + LF(LF_FX, li), ucy = (float)ciy + LF(LF_FY, li);
     const float xlo = ucx - rw - a_box - 0.01f, xhi = ucx + rw - a_box + (float)KB + 0.01f;
     const float ylo = ucy - rw - a_box - 0.01f, yhi = ucy + rw - a_box + (float)KB + 0.01f;
@@ -567,6 +661,8 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
                 : (kx0 >= -g.H && ky0 > -g.H && ky0 + KB - 1 <= g.H);
             if (interior) mf |= 1u << t; else me |= 1u << t;
             if (mirror) mneg |= 1u << t;
+          } else if (fold_col) {
+            md |= 1u << t;
           } else {
             mc |= 1u << t;
           }
@@ -603,6 +699,23 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
     qf += total & 1023;
     qe += (total >> 10) & 1023;
     qc += total >> 20;
+    // voxels of fold columns (rare: only footprints at x <= floor(a))
+    if (__any_sync(0xffffffffu, md != 0)) {
+      const int cd = __popc(md);
+      int incd = cd;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incd, o);
+        if (lane >= o) incd += v;
+      }
+      int pd = qd + incd - cd;
+      while (md) {
+        const int t = __ffs(md) - 1;
+        md &= md - 1;
+        s_qd[pd++] = base | (unsigned)t;
+      }
+      qd += __shfl_sync(0xffffffffu, incd, 31);
+    }
   };
 
   // drain the queues that hold a full round (every queue entirely if `all`);
@@ -611,6 +724,7 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
     if (qf >= 32 || (all && qf > 0)) drain(s_qf, qf, 0, all);
     if (qe >= 32 || (all && qe > 0)) drain(s_qe, qe, 1, all);
     if (qc >= 32 || (all && qc > 0)) drain(s_qc, qc, 2, all);
+    if (qd >= 32 || (all && qd > 0)) drain(s_qd, qd, 3, all);
   };
 
   const float *rot = args.rot;
@@ -688,7 +802,7 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
     ph[PH_WARP_CYCLES] = (unsigned long long)(clock64() - t_start);
     // queueing time = total minus the other phases
     unsigned long long other = ph[PH_CULL] + ph[PH_DRAIN_FAST] + ph[PH_DRAIN_EDGE] +
-                               ph[PH_DRAIN_CAREFUL] + ph[PH_FLUSH];
+                               ph[PH_DRAIN_CAREFUL] + ph[PH_DRAIN_FOLD] + ph[PH_FLUSH];
     ph[PH_QUEUE] = ph[PH_WARP_CYCLES] > other ? ph[PH_WARP_CYCLES] - other : 0;
 #pragma unroll
     for (int k = 0; k < PH_COUNT; ++k)

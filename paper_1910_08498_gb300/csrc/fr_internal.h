@@ -68,6 +68,7 @@ struct InsertArgs {
 enum PhaseCounter {
   PH_CULL = 0, PH_QUEUE, PH_DRAIN_FAST, PH_DRAIN_EDGE, PH_DRAIN_CAREFUL, PH_FLUSH,
   PH_ITEMS_FAST, PH_ITEMS_EDGE, PH_ITEMS_CAREFUL, PH_LIST_IMAGES, PH_WARP_CYCLES, PH_ROUNDS,
+  PH_DRAIN_FOLD, PH_ITEMS_FOLD,
   PH_COUNT = 16
 };
 
