@@ -310,6 +310,30 @@ def run_ours(args):
     best = rep_tune["best_config"]
     space_avg_ns = rep_tune["mean_ns_per_image"]
 
+    # ---- tuning with the learned search order (the shipped GB300 cost model;
+    # budget: a tenth of the space), same cold start
+    from paper_1910_08498_gb300 import costmodel
+    L.fr_reset(ctx)
+    L.fr_retune(ctx, True)
+    costmodel.load_pretrained(ctx)
+    L.fr_set_options(ctx, tuning=1, search=L.FR_SEARCH_LEARNED, steps_per_insert=4, forced_config=-1,
+                     budget=0)
+    ln_inserts, t_ln, u_ln = 0, 0.0, 0
+    while True:
+        dt, u, _ = timed_steps(1, ln_inserts)
+        t_ln += dt
+        u_ln += u
+        ln_inserts += 1
+        if L.fr_tuning_report(ctx)["tuned"] or ln_inserts >= 200:
+            break
+    rep_ln = L.fr_tuning_report(ctx)
+    best_ln = rep_ln["best_config"]
+    meas_map = {c: ns for c, ns, _ in meas}
+
+    # back to the exhaustive choice for the headline
+    L.fr_reset(ctx)
+    L.fr_set_options(ctx, tuning=0, forced_config=best)
+
     # ---- tuned (headline)
     timed_steps(args.warmup)
     barrier(world)
@@ -427,6 +451,20 @@ def run_ours(args):
                    "tuning_phase_value": u_tune / t_tune,
                    "per_config_ns_per_image": {L.fr_describe_config(c): round(ns, 1)
                                                for c, ns, _ in sorted(meas, key=lambda x: x[1])}},
+        "tuning_learned": {
+            "inserts": ln_inserts, "evaluated": rep_ln["evaluated"], "space": rep_ln["space_size"],
+            "best": L.fr_describe_config(best_ln), "overhead_pct": rep_ln["tuning_overhead_pct"],
+            "tuning_phase_value": u_ln / t_ln,
+            "regret_vs_exhaustive": (meas_map[best_ln] / meas_map[best] - 1.0)
+            if best_ln in meas_map and best in meas_map else None,
+            "model": "data/costmodel_gb300.json (trained on data/sweep_gb300_train.json)"},
+        "stream_overhead_pct": {
+            # the paper's overhead over a whole stream of 20 batches (Sec. 5.3.2):
+            # tuning inserts as measured, the rest at the tuned rate
+            "exhaustive": 100.0 * ((t_tune + max(0, 20 - tune_inserts) * t_tu / args.steps)
+                                   / (20 * t_tu / args.steps) - 1.0) if tune_inserts <= 20 else None,
+            "learned": 100.0 * ((t_ln + max(0, 20 - ln_inserts) * t_tu / args.steps)
+                                / (20 * t_tu / args.steps) - 1.0) if ln_inserts <= 20 else None},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,

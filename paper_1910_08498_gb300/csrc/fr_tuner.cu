@@ -146,7 +146,8 @@ std::vector<int> Tuner::search_order(const TuneKey &k, fr_ctx *c) {
   if (o.search == FR_SEARCH_LEARNED && c->mlp_trained) {
     int pb = -1;
     order = learned_order(c, k, valid, &pb);
-    int budget = o.budget > 0 ? o.budget : std::max(1, (int)std::ceil(0.1 * valid.size()));
+    // default budget: at most a tenth of the valid space
+    int budget = o.budget > 0 ? o.budget : std::max(1, (int)(valid.size() / 10));
     if ((int)order.size() > budget) order.resize(budget);
     keys_[k].predicted_best = pb;
     return order;
