@@ -1,0 +1,76 @@
+"""Parity at the benchmark's full size (S = 256, one batch of 5000 FP32
+images, the launch configurations bench.py times), on sampled voxels the
+oracle computes one by one (brute force over every pixel of every image),
+plus properties that hold at any size."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1910_08498_gb300 import _lib as L
+from paper_1910_08498_gb300 import inputs
+from tests.helpers import A32, ALPHA, TOL_F32
+
+pytestmark = pytest.mark.gpu
+
+S, N = 256, 5000
+
+
+@pytest.fixture(scope="module")
+def batch():
+    c = inputs.CONFIG_LARGE
+    img, rot = inputs.make_batch(S, N, c["seed"] * 1000)
+    return img, rot
+
+
+@pytest.fixture(scope="module")
+def samples(batch):
+    img, rot = batch
+    H = S // 2
+    rng = np.random.default_rng(11)
+    pts = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, -1), (2, -3, 1), (-2, 5, 7), (H, H, H),
+           (H, -H, 0), (0, H, -H), (-1, -H, H), (40, -60, 17), (100, 3, -90)]
+    # near the centre (many planes), in the fold columns, and random
+    pts += [tuple(int(v) for v in rng.integers(-6, 7, 3)) for _ in range(8)]
+    pts += [(int(rng.integers(-2, 2)), int(rng.integers(-H, H + 1)), int(rng.integers(-H, H + 1)))
+            for _ in range(6)]
+    pts += [(int(rng.integers(-2, H + 1)), int(rng.integers(-H, H + 1)), int(rng.integers(-H, H + 1)))
+            for _ in range(14)]
+    pts = [p for p in pts if p[0] >= -2]
+    Vo, Wo = oracle.voxels(S, img.numpy(), rot.numpy(), pts, a=A32, alpha=ALPHA)
+    return np.array(pts), Vo, Wo
+
+
+@pytest.mark.parametrize("cfg", [13, 4, 43])
+def test_full_size_sampled_voxels(batch, samples, cfg):
+    img, rot = batch
+    pts, Vo, Wo = samples
+    ctx = L.fr_create(S, A32, ALPHA, 0, 10000)
+    try:
+        if not L.fr_config_valid(ctx, cfg):
+            pytest.skip("configuration not valid here")
+        L.fr_set_options(ctx, tuning=0, forced_config=cfg)
+        L.fr_insert(ctx, img.cuda(), rot.cuda())
+        D = S + 1
+        V = torch.empty(D ** 3, dtype=torch.complex64, device="cuda")
+        W = torch.empty(D ** 3, dtype=torch.float32, device="cuda")
+        L.fr_finalize(ctx, V, W)
+        torch.cuda.synchronize()
+        assert L.fr_last_device_error(ctx) == L.FR_OK
+        # properties at full size: voxels x < -floor(a) untouched, W >= 0,
+        # total weight positive and finite
+        H = S // 2
+        Wg = W.view(D, D, D)
+        assert torch.count_nonzero(Wg[:, :, : H - 1]).item() == 0
+        assert torch.all(Wg >= 0).item() and torch.isfinite(V).all().item()
+        scale_v = V.abs().max().item()
+        scale_w = W.max().item()
+        idx = torch.tensor([((z + H) * D + (y + H)) * D + (x + H) for x, y, z in pts])
+        Vg = V[idx.cuda()].cpu().numpy().astype(np.complex128)
+        Wg = W[idx.cuda()].cpu().numpy().astype(np.float64)
+    finally:
+        L.fr_destroy(ctx)
+    ev = np.abs(Vg - Vo) / scale_v
+    ew = np.abs(Wg - Wo) / scale_w
+    assert ev.max() <= TOL_F32, (cfg, ev.max(), pts[int(ev.argmax())])
+    assert ew.max() <= TOL_F32, (cfg, ew.max(), pts[int(ew.argmax())])

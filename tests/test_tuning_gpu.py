@@ -1,0 +1,90 @@
+"""Dynamic tuning behaviour on the GPU (Sec. 3.2, Sec. 5.3): a key change
+(new batch-size bucket) starts a new tuning key and a return to an old key
+reuses its result; fr_retune forgets it; the tuning cache saved to JSON is
+restored by a new context, which then runs the cached best without
+evaluating anything.  Volumes stay those of the oracle throughout."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1910_08498_gb300 import _lib as L
+from paper_1910_08498_gb300 import inputs
+from tests.helpers import TOL_F32, oracle_insert, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _finalize(ctx, S):
+    D = S + 1
+    V = torch.empty(D ** 3, dtype=torch.complex64, device="cuda")
+    W = torch.empty(D ** 3, dtype=torch.float32, device="cuda")
+    L.fr_finalize(ctx, V, W)
+    torch.cuda.synchronize()
+    return V.cpu().numpy().astype(np.complex128), W.cpu().numpy().astype(np.float64)
+
+
+def _tune_until_done(ctx, img, rot, cap=60):
+    for _ in range(cap):
+        L.fr_insert(ctx, img, rot)
+        if L.fr_tuning_report(ctx)["tuned"]:
+            return
+    raise AssertionError("tuning did not finish")
+
+
+def test_key_change_retunes_and_returns_reuse(tmp_path):
+    S = 48
+    big = [t.cuda() for t in inputs.make_batch(S, 200, 70)]    # bucket floor(log2 200) = 7
+    small = [t.cuda() for t in inputs.make_batch(S, 20, 71)]   # bucket 4
+    ctx = L.fr_create(S)
+    try:
+        L.fr_set_options(ctx, tuning=1, search=L.FR_SEARCH_RANDOM, budget=6, steps_per_insert=3)
+        _tune_until_done(ctx, *big)
+        r1 = L.fr_tuning_report(ctx)
+        assert r1["evaluated"] == 6 and r1["n_bucket"] == 7
+        _tune_until_done(ctx, *small)
+        r2 = L.fr_tuning_report(ctx)
+        assert r2["n_bucket"] == 4 and r2["evaluated"] == 6 and r2["retunes"] >= r1["retunes"]
+        L.fr_insert(ctx, *big)          # back to the first key: cached, nothing new measured
+        r3 = L.fr_tuning_report(ctx)
+        assert r3["n_bucket"] == 7 and r3["tuned"] == 1 and r3["best_config"] == r1["best_config"]
+        assert r3["evaluated"] == r1["evaluated"]
+        L.fr_retune(ctx, 0)             # forget the current key: tuning starts over
+        r4 = L.fr_tuning_report(ctx)
+        assert r4["tuned"] == 0
+        path = str(tmp_path / "cache.json")
+        _tune_until_done(ctx, *big)
+        L.fr_tuning_save(ctx, path)
+        best = L.fr_tuning_report(ctx)["best_config"]
+    finally:
+        L.fr_destroy(ctx)
+
+    # a new context restores the cache and runs the cached best at once
+    ctx = L.fr_create(S)
+    try:
+        L.fr_set_options(ctx, tuning=1, search=L.FR_SEARCH_RANDOM, budget=6, steps_per_insert=3)
+        L.fr_tuning_load(ctx, path)
+        L.fr_insert(ctx, *big)
+        r = L.fr_tuning_report(ctx)
+        assert r["tuned"] == 1 and r["best_config"] == best and r["last_config"] == best
+        V, W = _finalize(ctx, S)
+    finally:
+        L.fr_destroy(ctx)
+    Vr, Wr, _ = oracle_insert(S, [(big[0].cpu(), big[1].cpu())])
+    assert rel_err(V, Vr) <= TOL_F32 and rel_err(W, Wr) <= TOL_F32
+
+
+def test_tuning_with_every_search_keeps_results():
+    S = 40
+    batches = [inputs.make_batch(S, 90, 80 + b) for b in range(5)]
+    Vr, Wr, _ = oracle_insert(S, batches)
+    for search in (L.FR_SEARCH_EXHAUSTIVE, L.FR_SEARCH_RANDOM):
+        ctx = L.fr_create(S)
+        try:
+            L.fr_set_options(ctx, tuning=1, search=search, budget=10, steps_per_insert=4)
+            for img, rot in batches:
+                L.fr_insert(ctx, img.cuda(), rot.cuda())
+            V, W = _finalize(ctx, S)
+            assert L.fr_tuning_report(ctx)["images"] == 450
+        finally:
+            L.fr_destroy(ctx)
+        assert rel_err(V, Vr) <= TOL_F32 and rel_err(W, Wr) <= TOL_F32
