@@ -643,8 +643,27 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
     const bool direct_all = xlo >= 1.f && xhi <= Hf && ylo >= -Hf && yhi <= Hf - 1.f;
     const bool mirror_all = xhi <= -1.f && xlo >= -Hf && ylo > -Hf && yhi <= Hf;
     if (fx0 > -g.xa0 && (direct_all || mirror_all)) {
-      mf = near;
-      mneg = mirror_all ? near : 0u;
+      // every near voxel is a fast item.  A column's near voxels are one run
+      // of z levels [t0, t0 + c), so the lane-major positions come from a
+      // prefix sum over lanes done with one ballot per bit of c (c <= 8), and
+      // the stores are predicated, without a loop
+      const int c = __popc(near);
+      const int t0 = near ? __ffs(near) - 1 : 0;
+      const unsigned lt = (1u << lane) - 1u;
+      int excl = 0, tot = 0;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const unsigned bal = __ballot_sync(0xffffffffu, (c >> b) & 1);
+        excl += __popc(bal & lt) << b;
+        tot += __popc(bal) << b;
+      }
+      const unsigned base = ((unsigned)li << 9) | (mirror_all ? 1u << 8 : 0u) | ((unsigned)lane << 3);
+      const int p0 = qf + excl - t0;
+#pragma unroll
+      for (int t = 0; t < ZC; ++t)
+        if ((near >> t) & 1u) s_qf[p0 + t] = base | (unsigned)t;
+      qf += tot;
+      return;
     } else {
       // phase 2: classify the near voxels one by one
       for (unsigned m = near; m; m &= m - 1) {
