@@ -18,6 +18,10 @@ Phases (one JSON line at the end):
   e2e      the tuned path with host-resident (pinned) inputs copied in every
            step, the device status word read back every step, and the final
            volume downloaded once at the end of the timed region;
+  fp16     the tuned configuration on FP16-stored copies of the batches;
+  stream   20 batches with a switch to S = 192 for batches 8-11 (Sec. 5.3.2
+           style): tuning overhead against the oraculum, exhaustive and
+           learned search, with and without the tuning cache;
   batched  the uneven-batch workload (40 batches of S in {64..256}, n in
            [500, 5000]): one persistent-gather graph replay per pass against
            one fr_insert per batch.
@@ -59,6 +63,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the uneven-batch workload")
+    p.add_argument("--no-stream", action="store_true", help="skip the 20-batch stream with an S switch")
+    p.add_argument("--no-fp16", action="store_true", help="skip the FP16-image measurement")
     p.add_argument("--only-batched", action="store_true",
                    help="profiling mode: run only the uneven-batch workload and print its result")
     p.add_argument("--seed", type=int, default=5)
@@ -423,6 +429,32 @@ def run_ours(args):
             "peak_note": f"FP32 FMA peak: {sms} SMs x 128 lanes x 2 flops x {max_mhz:.0f} MHz (max SM clock)",
             "avg_launch_ms": 1e3 * per_launch_s, "updates_per_launch": ups_per_launch}
 
+    # ---- FP16-stored images, the tuned configuration
+    fp16 = None
+    if not f16 and not args.no_fp16:
+        h16 = [(inputs.to_half(img), rot) for img, rot in batches[:2]]
+        ctx16 = L.fr_create(S, a, 15.0, 0, 10000)
+        L.fr_set_options(ctx16, tuning=0, forced_config=best)
+        for i in range(args.warmup):
+            L.fr_insert(ctx16, *h16[i % 2])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(args.steps):
+            L.fr_insert(ctx16, *h16[i % 2])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t16 = e0.elapsed_time(e1) / 1e3
+        fp16 = {"value": sum(updates[i % 2] for i in range(args.steps)) / t16, "unit": UNIT,
+                "config": L.fr_describe_config(best), "ms_per_step": 1e3 * t16 / args.steps}
+        L.fr_destroy(ctx16)
+        del h16
+
+    stream_exp = None
+    if not args.no_stream:
+        stream_exp = run_stream(L, inputs, costmodel, dev, stream, batches, updates, n, f16,
+                                args.seed * 1000 + 500 + rank)
+
     batched = None
     if not args.no_batched:
         batched = run_batched(L, inputs, dev, stream, max(2, args.steps // 3), 1, f16)
@@ -468,6 +500,8 @@ def run_ours(args):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "fp16": fp16,
+        "stream": stream_exp,
         "batched": batched,
         "gpu_launches": args.steps * launches_per_insert(L, best, n),
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
@@ -532,6 +566,87 @@ def run_batched(L, inputs, dev, stream, steps, warmup, f16):
     return {"workload": f"{len(spec)} batches, S in {sizes}, n in [500, 5000] (seeded), one volume each, "
                         f"{'FP16' if f16 else 'FP32'} images",
             "updates_per_pass": ups, "images_per_pass": sum(n for _, n, _ in spec), **out}
+
+
+def run_stream(L, inputs, costmodel, dev, stream, batches256, updates256, n, f16, seed):
+    """The paper's stream experiment (Sec. 5.3.2) on synthetic inputs: 20
+    batches of n images, S = 256 except batches 8-11 at S = 192.  Each S has
+    its own context (its own volume).  T_dyn: cold-start tuning during the
+    stream (exhaustive or learned search), with the tuning cache (the S = 256
+    context keeps its result over the switch) or without it (its key is
+    forgotten when S changes back).  T_oraculum: every batch with the best
+    configuration measured for its S from the start.  Overhead =
+    T_dyn / T_oraculum - 1."""
+    import torch
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    b192 = []
+    for _ in range(2):
+        rot = inputs.random_rotations(n, gen, dev).contiguous()
+        img = inputs.random_images(192, n, gen, dev)
+        b192.append((inputs.to_half(img) if f16 else img.contiguous(), rot))
+    plan = [(256, i % len(batches256)) for i in range(8)] + [(192, i % 2) for i in range(4)] + \
+           [(256, (8 + i) % len(batches256)) for i in range(8)]
+
+    def run(ctxs, forget_on_return):
+        ev = []
+        prev = None
+        for S, b in plan:
+            c = ctxs[S]
+            if forget_on_return and prev == 192 and S == 256:
+                L.fr_retune(c, 1)
+            img, rot = (batches256 if S == 256 else b192)[b]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            L.fr_insert(c, img, rot)
+            e1.record(stream)
+            ev.append((e0, e1))
+            prev = S
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / 1e3
+
+    def contexts(search):
+        cs = {}
+        for S in (256, 192):
+            c = L.fr_create(S, 1.9, 15.0, 0, 10000)
+            if search == L.FR_SEARCH_LEARNED:
+                costmodel.load_pretrained(c)
+            L.fr_set_options(c, tuning=1, search=search, steps_per_insert=4, budget=0, forced_config=-1)
+            cs[S] = c
+        return cs
+
+    out = {}
+    best = {}
+    for name, search in (("exhaustive", L.FR_SEARCH_EXHAUSTIVE), ("learned", L.FR_SEARCH_LEARNED)):
+        for cache in (True, False):
+            cs = contexts(search)
+            t = run(cs, forget_on_return=not cache)
+            for c in cs.values():
+                L.fr_destroy(c)
+            out[f"{name}_{'cache' if cache else 'no_cache'}_s"] = t
+    # oraculum: the exhaustive best of each S (tuned to the end outside the
+    # stream) from the first batch
+    cs = contexts(L.FR_SEARCH_EXHAUSTIVE)
+    for S, c in cs.items():
+        img, rot = (batches256 if S == 256 else b192)[0]
+        for _ in range(100):
+            L.fr_insert(c, img, rot)
+            if L.fr_tuning_report(c)["tuned"]:
+                break
+        best[S] = L.fr_tuning_report(c)["best_config"]
+        L.fr_set_options(c, tuning=0, forced_config=best[S])
+    run(cs, False)  # warm
+    for c in cs.values():
+        L.fr_reset(c)
+    t_or = run(cs, False)
+    for c in cs.values():
+        L.fr_destroy(c)
+    res = {"batches": len(plan), "images": len(plan) * n, "oraculum_s": t_or,
+           "oraculum_configs": {S: L.fr_describe_config(b) for S, b in best.items()}}
+    for k, v in out.items():
+        res[k] = v
+        res[k.replace("_s", "_overhead_pct")] = 100.0 * (v / t_or - 1.0)
+    return res
 
 
 def launches_per_insert(L, cfg, n):
