@@ -18,6 +18,7 @@ Phases (one JSON line at the end):
   e2e      the tuned path with host-resident (pinned) inputs copied in every
            step, the device status word read back every step, and the final
            volume downloaded once at the end of the timed region;
+  recon    Algorithm 1's last step on the accumulated volume (fr_reconstruct);
   fp16     the tuned configuration on FP16-stored copies of the batches;
   stream   20 batches with a switch to S = 192 for batches 8-11 (Sec. 5.3.2
            style): tuning overhead against the oraculum, exhaustive and
@@ -65,6 +66,7 @@ def parse():
     p.add_argument("--no-batched", action="store_true", help="skip the uneven-batch workload")
     p.add_argument("--no-stream", action="store_true", help="skip the 20-batch stream with an S switch")
     p.add_argument("--no-fp16", action="store_true", help="skip the FP16-image measurement")
+    p.add_argument("--no-recon", action="store_true", help="skip the reconstruction (last step) timing")
     p.add_argument("--only-batched", action="store_true",
                    help="profiling mode: run only the uneven-batch workload and print its result")
     p.add_argument("--seed", type=int, default=5)
@@ -429,6 +431,28 @@ def run_ours(args):
             "peak_note": f"FP32 FMA peak: {sms} SMs x 128 lanes x 2 flops x {max_mhz:.0f} MHz (max SM clock)",
             "avg_launch_ms": 1e3 * per_launch_s, "updates_per_launch": ups_per_launch}
 
+    # ---- Algorithm 1's last step on the accumulated volume: symmetrise,
+    # weight, inverse FFT (fr_reconstruct)
+    recon = None
+    if not args.no_recon:
+        out = torch.empty(S ** 3, dtype=torch.float32, device=dev)
+        L.fr_reconstruct(ctx, out, 1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k = max(3, args.steps)
+        e0.record(stream)
+        for _ in range(k):
+            L.fr_reconstruct(ctx, out, 1.0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        nspec = S * S * (S // 2 + 1)
+        recon = {"ms_per_call": ms, "S": S, "spectrum_entries": nspec,
+                 "weighting_bytes": nspec * (24 + 8),
+                 "note": "weighting kernel (reads the double-float sums, writes the half spectrum) "
+                         "+ cuFFT C2R of S^3"}
+        del out
+
     # ---- FP16-stored images, the tuned configuration
     fp16 = None
     if not f16 and not args.no_fp16:
@@ -501,6 +525,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "fp16": fp16,
+        "reconstruct": recon,
         "stream": stream_exp,
         "batched": batched,
         "gpu_launches": args.steps * launches_per_insert(L, best, n),

@@ -175,6 +175,23 @@ int fr_insert_batched(fr_ctx *const *ctxs, const void *const *images, const fr_d
  * (synchronising the stream). */
 int fr_finalize(fr_ctx *ctx, void *V, float *W, void *stream);
 
+/* The last step of Algorithm 1 (Sec. 5.3.1): apply the weights W to G and
+ * transform back, from the context's accumulated sums.  With V, W the raw
+ * sums of fr_finalize:
+ *     Vs(v) = V(v) + conj(V(-v)),  Ws(v) = W(v) + W(-v)  (undo the fold)
+ *     F(k)  = Vs(k) / max(Ws(k), w_clip) / S^3,  k in [-S/2, S/2)^3,
+ *             F = 0 on the Nyquist planes kx = S/2, ky = -S/2, kz = -S/2
+ *     out   = the real inverse DFT of F: out[z][y][x] (float32, S^3, device,
+ *             x fastest, origin at index 0) = sum_k F(k) exp(2 pi i k.r / S)
+ * The paper does not spell the weighting out; the clip w_clip > 0 (1 is a
+ * good value: a voxel met by about one blob of weight keeps its sum) keeps
+ * the division away from zero.  Allocates, on first use, a half-spectrum
+ * buffer (8 S^2 (S/2+1) bytes) and an inverse-FFT plan; the inverse FFT is
+ * the CUDA toolkit's cuFFT, loaded at run time (FR_ERR_UNSUPPORTED if it
+ * cannot be loaded).  Work is enqueued on `stream`.  Returns FR_OK,
+ * FR_ERR_INVALID_ARG (null pointer, w_clip <= 0), FR_ERR_OOM, FR_ERR_CUDA. */
+int fr_reconstruct(fr_ctx *ctx, float *out, float w_clip, void *stream);
+
 /* ---------------------------------------------------------------- tuning */
 
 /* Forget the tuning results of the current key (or of every key if all != 0);

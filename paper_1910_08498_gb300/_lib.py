@@ -123,6 +123,7 @@ def _lib():
             "fr_mlp_get": (i, [vp, P(f)]),
             "fr_mlp_set": (i, [vp, P(f)]),
             "fr_insert_noalloc": (i, [i, f, f, vp, i, vp, i, vp, vp, vp]),
+            "fr_reconstruct": (i, [vp, vp, f, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -204,6 +205,14 @@ def fr_insert_noalloc(S, images, rotations, V, W, a=1.9, alpha=15.0, n=None, str
     return _check(_lib().fr_insert_noalloc(int(S), float(a), float(alpha), _ptr(images),
                                            _dtype_of(images), _ptr(rotations), int(n), _ptr(V),
                                            _ptr(W), _stream(stream)), "fr_insert_noalloc")
+
+
+def fr_reconstruct(ctx, out, w_clip=1.0, stream=None):
+    """Weighted inverse transform of the context's volume into out (CUDA
+    float32, S^3, [z][y][x])."""
+    assert out.is_cuda and out.is_contiguous() and out.dtype.is_floating_point
+    return _check(_lib().fr_reconstruct(ctx, _ptr(out), float(w_clip), _stream(stream)),
+                  "fr_reconstruct")
 
 
 def fr_insert_batched(ctxs, images, rotations, ns=None, capture=0, stream=None):

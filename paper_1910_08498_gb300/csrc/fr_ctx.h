@@ -40,6 +40,10 @@ struct fr_ctx {
   // cost model
   float *d_mlp = nullptr;
   bool mlp_trained = false;
+  // reconstruction (Algorithm 1's last step): weighted half spectrum and the
+  // inverse-FFT plan, created on first use
+  float2 *spec = nullptr;
+  int fft_plan = -1;
 };
 
 
@@ -57,6 +61,8 @@ double gather_unit_loads(const fr_ctx *c, int shape, int n, double target,
                          std::vector<UnitLoad> &out, int &any_split);
 // drop cached batched-insertion plans that refer to c (called by fr_destroy)
 void batched_forget(const fr_ctx *c);
+// release the reconstruction buffers of c (called by fr_destroy)
+void reconstruct_release(fr_ctx *c);
 int do_insert_ctx(fr_ctx *c, const void *images, fr_dtype dtype, const float *rot, int n,
                   cudaStream_t st);
 }  // namespace fr

@@ -1,0 +1,143 @@
+// fr_reconstruct.cu -- the last step of Algorithm 1 (Sec. 5.3.1) on the GPU:
+// apply the weights W to G and transform back.  The weighting kernel is this
+// library's; the inverse FFT is the vendor's plain C2R transform (cuFFT),
+// loaded at run time so that libfr.so does not depend on it.
+//
+//   Vs(v) = V(v) + conj(V(-v)),  Ws(v) = W(v) + W(-v)   (undo the half-space fold)
+//   F(k)  = Vs(k) / max(Ws(k), w_clip) / S^3              k in [-S/2, S/2)^3,
+//           0 on the Nyquist planes k_x = S/2, k_y = -S/2, k_z = -S/2
+//   f     = inverse DFT of F (real, S^3, origin at index 0)
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <dlfcn.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "../../include/fr.h"
+#include "fr_ctx.h"
+#include "fr_internal.h"
+
+namespace fr {
+namespace {
+
+// Half spectrum in C2R order: [kz][ky][kx], kz and ky in FFT order (index j
+// is frequency j for j < S/2, j - S otherwise), kx = 0 .. S/2.
+__global__ void weight_kernel(const Geom g, const float *__restrict__ acc, size_t plane,
+                              float w_clip, float inv_n, float2 *__restrict__ F) {
+  const int NXh = g.H + 1;
+  const size_t total = (size_t)g.S * g.S * NXh;
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < total;
+       o += (size_t)gridDim.x * blockDim.x) {
+    const int kx = (int)(o % NXh);
+    const size_t r = o / NXh;
+    const int jy = (int)(r % g.S), jz = (int)(r / g.S);
+    const int ky = jy < g.H ? jy : jy - g.S, kz = jz < g.H ? jz : jz - g.S;
+    float2 out = make_float2(0.f, 0.f);
+    if (kx != g.H && ky != -g.H && kz != -g.H) {
+      const size_t v = ((size_t)(kz + g.H) * g.D + (size_t)(ky + g.H)) * g.NXa + (size_t)(kx - g.xa0);
+      float re = acc[v] + acc[3 * plane + v];
+      float im = acc[plane + v] + acc[4 * plane + v];
+      float w = acc[2 * plane + v] + acc[5 * plane + v];
+      if (-kx >= g.xa0) {  // -v is stored too: its conjugate joins
+        const size_t m =
+            ((size_t)(-kz + g.H) * g.D + (size_t)(-ky + g.H)) * g.NXa + (size_t)(-kx - g.xa0);
+        re += acc[m] + acc[3 * plane + m];
+        im -= acc[plane + m] + acc[4 * plane + m];
+        w += acc[2 * plane + m] + acc[5 * plane + m];
+      }
+      const float s = inv_n / fmaxf(w, w_clip);
+      out = make_float2(re * s, im * s);
+    }
+    F[o] = out;
+  }
+}
+
+// cuFFT entry points, resolved once
+struct Cufft {
+  bool tried = false, ok = false;
+  cufftResult (*plan3d)(cufftHandle *, int, int, int, cufftType) = nullptr;
+  cufftResult (*set_stream)(cufftHandle, cudaStream_t) = nullptr;
+  cufftResult (*exec_c2r)(cufftHandle, cufftComplex *, cufftReal *) = nullptr;
+  cufftResult (*destroy)(cufftHandle) = nullptr;
+};
+std::mutex g_fft_mu;
+Cufft g_fft;
+
+const Cufft &cufft() {
+  std::lock_guard<std::mutex> lk(g_fft_mu);
+  if (g_fft.tried) return g_fft;
+  g_fft.tried = true;
+  const char *names[] = {"libcufft.so.12", "libcufft.so", "/usr/local/cuda/lib64/libcufft.so.12"};
+  void *h = nullptr;
+  for (const char *n : names)
+    if ((h = dlopen(n, RTLD_NOW | RTLD_GLOBAL)) != nullptr) break;
+  if (!h) return g_fft;
+  g_fft.plan3d = reinterpret_cast<decltype(g_fft.plan3d)>(dlsym(h, "cufftPlan3d"));
+  g_fft.set_stream = reinterpret_cast<decltype(g_fft.set_stream)>(dlsym(h, "cufftSetStream"));
+  g_fft.exec_c2r = reinterpret_cast<decltype(g_fft.exec_c2r)>(dlsym(h, "cufftExecC2R"));
+  g_fft.destroy = reinterpret_cast<decltype(g_fft.destroy)>(dlsym(h, "cufftDestroy"));
+  g_fft.ok = g_fft.plan3d && g_fft.set_stream && g_fft.exec_c2r && g_fft.destroy;
+  return g_fft;
+}
+
+}  // namespace
+
+void reconstruct_release(fr_ctx *c) {
+  if (c->fft_plan >= 0 && g_fft.ok) g_fft.destroy((cufftHandle)c->fft_plan);
+  c->fft_plan = -1;
+  cudaFree(c->spec);
+  c->spec = nullptr;
+}
+
+}  // namespace fr
+
+using namespace fr;
+
+extern "C" int fr_reconstruct(fr_ctx *c, float *out, float w_clip, void *stream) {
+  if (!c || !out || !(w_clip > 0.f)) return FR_ERR_INVALID_ARG;
+  const Cufft &fft = cufft();
+  if (!fft.ok) return FR_ERR_UNSUPPORTED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Geom &g = c->g;
+  const size_t nspec = (size_t)g.S * g.S * (g.H + 1);
+  if (!c->spec) {
+    cudaError_t e = cudaMalloc(&c->spec, nspec * sizeof(float2));
+    if (e != cudaSuccess) {
+      fr_note_cuda_error((int)e);
+      return FR_ERR_OOM;
+    }
+  }
+  if (c->fft_plan < 0) {
+    cufftHandle h = 0;
+    if (fft.plan3d(&h, g.S, g.S, g.S, CUFFT_C2R) != CUFFT_SUCCESS) return FR_ERR_CUDA;
+    c->fft_plan = (int)h;
+  }
+  // the insertions enqueued on another stream must be complete
+  if (c->last_stream && c->last_stream != st) {
+    cudaError_t e = cudaStreamSynchronize(c->last_stream);
+    if (e != cudaSuccess) {
+      fr_note_cuda_error((int)e);
+      return FR_ERR_CUDA;
+    }
+  }
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int threads = 256;
+  const size_t want = (nspec + threads - 1) / threads;
+  const int blocks = (int)std::min<size_t>(want, (size_t)std::max(sms, 1) * 8);
+  const float inv_n = 1.0f / ((float)g.S * (float)g.S * (float)g.S);
+  weight_kernel<<<blocks, threads, 0, st>>>(g, c->acc, c->plane, w_clip, inv_n, c->spec);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    fr_note_cuda_error((int)e);
+    return FR_ERR_CUDA;
+  }
+  if (fft.set_stream((cufftHandle)c->fft_plan, st) != CUFFT_SUCCESS) return FR_ERR_CUDA;
+  if (fft.exec_c2r((cufftHandle)c->fft_plan, reinterpret_cast<cufftComplex *>(c->spec), out) !=
+      CUFFT_SUCCESS)
+    return FR_ERR_CUDA;
+  c->last_stream = st;
+  return FR_OK;
+}

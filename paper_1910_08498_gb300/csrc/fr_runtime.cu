@@ -456,6 +456,7 @@ int fr_destroy(fr_ctx *c) {
   if (!c) return FR_OK;
   cudaDeviceSynchronize();
   batched_forget(c);
+  reconstruct_release(c);
   c->tuner.release();
   cudaFree(c->acc);
   cudaFree(c->lut);
