@@ -18,7 +18,9 @@ Phases (one JSON line at the end):
   e2e      the tuned path with host-resident (pinned) inputs copied in every
            step, the device status word read back every step, and the final
            volume downloaded once at the end of the timed region;
-  recon    Algorithm 1's last step on the accumulated volume (fr_reconstruct);
+  recon    Algorithm 1's last step on the accumulated volume (fr_reconstruct)
+           and its image-side step, the images' 2D transforms staged into
+           the insertion input (fr_prepare_images);
   fp16     the tuned configuration on FP16-stored copies of the batches;
   stream   20 batches with a switch to S = 192 for batches 8-11 (Sec. 5.3.2
            style): tuning overhead against the oraculum, exhaustive and
@@ -453,6 +455,31 @@ def run_ours(args):
                          "+ cuFFT C2R of S^3"}
         del out
 
+    # ---- the image-side step: 2D transforms of n real images staged into the
+    # insertion input (fr_prepare_images), FP32 and FP16 output
+    prep = None
+    if not args.no_recon:
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(args.seed * 1000 + 900 + rank)
+        real = torch.randn(n, S, S, generator=gen, device=dev, dtype=torch.float32)
+        prep = {"images": n, "S": S}
+        for name, buf in (("f32", torch.empty(n, S, S // 2 + 1, dtype=torch.complex64, device=dev)),
+                          ("f16", torch.empty(n, S, S // 2 + 1, 2, dtype=torch.float16, device=dev))):
+            L.fr_prepare_images(ctx, real, buf, center=True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                L.fr_prepare_images(ctx, real, buf, center=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 3
+            byts = real.numel() * 4 + buf.numel() * buf.element_size()
+            prep[name] = {"ms_per_batch": ms, "images_per_s": n / (ms * 1e-3),
+                          "hbm_gbs_min_traffic": byts / (ms * 1e-3) / 1e9}
+            del buf
+        del real
+
     # ---- FP16-stored images, the tuned configuration
     fp16 = None
     if not f16 and not args.no_fp16:
@@ -526,6 +553,7 @@ def run_ours(args):
         "e2e": e2e,
         "fp16": fp16,
         "reconstruct": recon,
+        "prepare_images": prep,
         "stream": stream_exp,
         "batched": batched,
         "gpu_launches": args.steps * launches_per_insert(L, best, n),

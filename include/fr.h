@@ -175,6 +175,25 @@ int fr_insert_batched(fr_ctx *const *ctxs, const void *const *images, const fr_d
  * (synchronising the stream). */
 int fr_finalize(fr_ctx *ctx, void *V, float *W, void *stream);
 
+/* The image-side step of Algorithm 1 (Sec. 5.3.1; the paper runs it on the
+ * CPU and uploads the result): the 2D Fourier transforms of n real images,
+ * written in the insertion's input layout and dtype, ready for fr_insert.
+ *   real   device float32 [n][S][S] (x fastest), 16-byte aligned; S is the
+ *          context's.
+ *   out    device [n][S][S/2+1] complex of `dtype` (fr_insert's layout), 16-byte
+ *          aligned: out[i][j][kx] = sum_{y,x} real[i][y][x] exp(-2 pi i (kx x +
+ *          ky y) / S), ky = j for j < S/2 and j - S otherwise (numpy's rfft2),
+ *          times (-1)^(kx + j) when center != 0 (the image origin taken at
+ *          pixel (S/2, S/2) instead of (0, 0)); FR_F16 rounds to nearest half.
+ *   n      0 <= n <= 2^24 (0: nothing).
+ * The transforms are the CUDA toolkit's cuFFT (batched R2C, loaded at run
+ * time; FR_ERR_UNSUPPORTED if it cannot be loaded), in chunks of 256 images;
+ * the sign and the FP16 conversion are a kernel of this library.  Allocates on
+ * first use the plans and, for FR_F16, a staging buffer of 256 transforms.
+ * Work is enqueued on `stream`. */
+int fr_prepare_images(fr_ctx *ctx, const float *real, int n, int center, void *out,
+                      fr_dtype dtype, void *stream);
+
 /* The last step of Algorithm 1 (Sec. 5.3.1): apply the weights W to G and
  * transform back, from the context's accumulated sums.  With V, W the raw
  * sums of fr_finalize:

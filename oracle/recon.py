@@ -1,6 +1,8 @@
-"""FP64 reference of the last step of Algorithm 1 (Sec. 5.3.1): apply the
-weights W to G and transform back -- TEST INFRASTRUCTURE ONLY (tests, smoke
-and the benchmark's CPU legs may import it; the product never does).
+"""FP64 references of the FFT steps of Algorithm 1 (Sec. 5.3.1) around the
+insertion: the images' forward transforms (image_spectra) and the last step,
+applying the weights W to G and transforming back (reconstruct) -- TEST
+INFRASTRUCTURE ONLY (tests, smoke and the benchmark's CPU legs may import
+it; the product never does).
 
 Readings (the paper does not spell the step out): the half-space fold is
 undone by Hermitian symmetrisation, Vs(v) = V(v) + conj(V(-v)) and
@@ -39,3 +41,13 @@ def reconstruct(S, V, W, w_clip=1.0):
     Vs, Ws = symmetrise(S, V, W)
     F = Vs / np.maximum(Ws, w_clip)
     return np.fft.irfftn(half_spectrum(S, F), s=(S, S, S), axes=(0, 1, 2))
+
+
+def image_spectra(real, center=False):
+    """FP64 2D transforms of real images [n][S][S] in the insertion's layout
+    [n][S][S/2+1] (numpy's rfft2); with center, the image origin is taken at
+    pixel (S/2, S/2) (equivalently, the spectrum times (-1)^(kx + j))."""
+    real = np.asarray(real, dtype=np.float64)
+    if center:
+        real = np.fft.ifftshift(real, axes=(-2, -1))
+    return np.fft.rfft2(real, axes=(-2, -1))

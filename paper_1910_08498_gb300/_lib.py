@@ -124,6 +124,7 @@ def _lib():
             "fr_mlp_set": (i, [vp, P(f)]),
             "fr_insert_noalloc": (i, [i, f, f, vp, i, vp, i, vp, vp, vp]),
             "fr_reconstruct": (i, [vp, vp, f, vp]),
+            "fr_prepare_images": (i, [vp, vp, i, i, vp, i, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -205,6 +206,16 @@ def fr_insert_noalloc(S, images, rotations, V, W, a=1.9, alpha=15.0, n=None, str
     return _check(_lib().fr_insert_noalloc(int(S), float(a), float(alpha), _ptr(images),
                                            _dtype_of(images), _ptr(rotations), int(n), _ptr(V),
                                            _ptr(W), _stream(stream)), "fr_insert_noalloc")
+
+
+def fr_prepare_images(ctx, real, out, center=False, n=None, stream=None):
+    """2D FFTs of real images [n,S,S] (CUDA float32) into out: complex64
+    [n,S,S/2+1] (or float32 [...,2]) for FP32, float16 [n,S,S/2+1,2] for FP16."""
+    if n is None:
+        n = real.shape[0]
+    assert real.is_cuda and out.is_cuda and real.is_contiguous() and out.is_contiguous()
+    return _check(_lib().fr_prepare_images(ctx, _ptr(real), int(n), int(bool(center)), _ptr(out),
+                                           _dtype_of(out), _stream(stream)), "fr_prepare_images")
 
 
 def fr_reconstruct(ctx, out, w_clip=1.0, stream=None):

@@ -44,6 +44,10 @@ struct fr_ctx {
   // inverse-FFT plan, created on first use
   float2 *spec = nullptr;
   int fft_plan = -1;
+  // image transforms: batched R2C plans (full chunk, tail) and the FP16 staging buffer
+  int prep_plan[2] = {-1, -1};
+  int prep_batch[2] = {0, 0};
+  float2 *prep_ws = nullptr;
 };
 
 

@@ -84,3 +84,26 @@ def test_nyquist_planes_are_dropped():
     # what survives is only the symmetrised image of those planes at k = +S/2 in y, z,
     # which lies outside [-S/2, S/2)^3
     assert np.max(np.abs(f)) == 0.0
+
+
+def test_image_spectra_closed_forms():
+    S = 8
+    # a unit impulse at the origin: flat spectrum; at the centre with
+    # center=True: flat as well (the origin is moved there)
+    d = np.zeros((1, S, S))
+    d[0, 0, 0] = 1.0
+    assert np.allclose(recon.image_spectra(d), 1.0)
+    c = np.zeros((1, S, S))
+    c[0, S // 2, S // 2] = 1.0
+    assert np.allclose(recon.image_spectra(c, center=True), 1.0)
+    # without centring, the centre impulse gives (-1)^(kx + ky), written out
+    F = recon.image_spectra(c)[0]
+    j = np.arange(S)[:, None]
+    kx = np.arange(S // 2 + 1)[None, :]
+    assert np.allclose(F, (-1.0) ** (kx + j))
+    # a single cosine along x of frequency 2: two bins of value S^2 / 2 at kx = 2, ky = 0
+    y, x = np.meshgrid(np.arange(S), np.arange(S), indexing="ij")
+    F = recon.image_spectra(np.cos(2 * np.pi * 2 * x / S)[None])[0]
+    ref = np.zeros_like(F)
+    ref[0, 2] = S * S / 2
+    assert np.allclose(F, ref, atol=1e-12)
