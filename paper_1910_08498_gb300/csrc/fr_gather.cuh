@@ -145,21 +145,28 @@ __device__ __forceinline__ void box_poly_interior(const InsertArgs &args, const 
   const int row_bytes = g.NX * ESZ;
   const int step = sgn * ESZ;
   const int col0 = sgn * kx0 * ESZ;
+  // all pixel loads first (they do not depend on the weights), then the math
+  float2 px[KB * KB];
+#pragma unroll
+  for (int l = 0; l < KB; ++l) {
+    int ky = sgn * (ky0 + l);
+    ky += ky < 0 ? g.S : 0;
+    const unsigned char *row = ibase + (ky * row_bytes + col0);
+#pragma unroll
+    for (int j = 0; j < KB; ++j) px[l * KB + j] = ld_px<F16>(row + j * step);
+  }
   float ar = sr, ai = si, aw = sw;
 #pragma unroll
   for (int l = 0; l < KB; ++l) {
     const float dy = fy - (float)l;
     const float ry = fmaf(dy, dy, uz2);
-    int ky = sgn * (ky0 + l);
-    ky += ky < 0 ? g.S : 0;
-    const unsigned char *row = ibase + (ky * row_bytes + col0);
 #pragma unroll
     for (int j = 0; j < KB; ++j) {
       const float dx = fx - (float)j;
       const float r2 = fmaf(dx, dx, ry);
       const float pv = poly_eo(c, fmaf(r2, two_inv_a2, -1.0f));
       const float w = r2 <= g.a2 ? pv : 0.0f;
-      const float2 p = ld_px<F16>(row + j * step);
+      const float2 p = px[l * KB + j];
       ar = fmaf(w, p.x, ar);
       ai = fmaf(w, p.y, ai);
       aw += w;
