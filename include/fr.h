@@ -88,7 +88,9 @@ typedef struct fr_ctx fr_ctx;
 typedef enum fr_search {
     FR_SEARCH_EXHAUSTIVE = 0, /* every valid configuration once, in a seeded order */
     FR_SEARCH_RANDOM = 1,     /* `budget` configurations drawn without replacement */
-    FR_SEARCH_LEARNED = 2     /* the cost model ranks the space; its top `budget` are measured */
+    FR_SEARCH_LEARNED = 2,    /* the cost model ranks the space; its top `budget` are measured */
+    FR_SEARCH_ANNEALING = 3,  /* simulated annealing over neighbouring configurations */
+    FR_SEARCH_MCMC = 4        /* Metropolis walk (constant temperature) over neighbours */
 } fr_search;
 
 typedef struct fr_options {
@@ -290,6 +292,20 @@ int fr_debug_phase_counters(fr_ctx *ctx, unsigned long long *out, int cap);
  * into out (device float[m]): mode 0 the table, mode 1 the Abramowitz & Stegun
  * Bessel approximations, mode 2 the register polynomial.  Test hook. */
 int fr_debug_blob(const fr_ctx *ctx, const float *r2, int m, int mode, float *out, void *stream);
+
+/* Host-only simulation of a search order over a table of known times, to
+ * compare searchers at equal budgets on measured sweeps.  ns_per_image:
+ * host double[nconfig] (nconfig must equal fr_num_configs(); a value <= 0
+ * marks an invalid configuration); budget >= 1 distinct configurations;
+ * start: the configuration an adaptive walk starts from (any invalid value:
+ * a random valid one); order: host int[budget] receives the configurations
+ * in the order the searcher measures them (adaptive searchers see each
+ * time as soon as they propose it).  search: FR_SEARCH_EXHAUSTIVE, _RANDOM,
+ * _ANNEALING or _MCMC (the learned order needs the model: see
+ * fr_mlp_forward).  Returns the number of configurations written, or a
+ * negative fr_status.  Touches no device. */
+int fr_search_simulate(int search, const double *ns_per_image, int nconfig, int budget,
+                       uint64_t seed, int start, int *order);
 
 /* ---------------------------------------------------------------- learned tuner */
 

@@ -22,7 +22,7 @@ FR_ERR_LAUNCH, FR_ERR_DEVICE_ASSERT, FR_ERR_TIMEOUT, FR_ERR_IO, FR_ERR_STATE = 5
 FR_ERR_NOALLOC_LIMIT = 10
 FR_NOALLOC_MAX_S = 64
 FR_F32, FR_F16 = 0, 1
-FR_SEARCH_EXHAUSTIVE, FR_SEARCH_RANDOM, FR_SEARCH_LEARNED = 0, 1, 2
+FR_SEARCH_EXHAUSTIVE, FR_SEARCH_RANDOM, FR_SEARCH_LEARNED, FR_SEARCH_ANNEALING, FR_SEARCH_MCMC = 0, 1, 2, 3, 4
 MLP_NPARAM = 5313
 
 
@@ -125,6 +125,7 @@ def _lib():
             "fr_insert_noalloc": (i, [i, f, f, vp, i, vp, i, vp, vp, vp]),
             "fr_reconstruct": (i, [vp, vp, f, vp]),
             "fr_prepare_images": (i, [vp, vp, i, i, vp, i, vp]),
+            "fr_search_simulate": (i, [i, P(d), i, i, ctypes.c_uint64, i, P(i)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -206,6 +207,18 @@ def fr_insert_noalloc(S, images, rotations, V, W, a=1.9, alpha=15.0, n=None, str
     return _check(_lib().fr_insert_noalloc(int(S), float(a), float(alpha), _ptr(images),
                                            _dtype_of(images), _ptr(rotations), int(n), _ptr(V),
                                            _ptr(W), _stream(stream)), "fr_insert_noalloc")
+
+
+def fr_search_simulate(search, ns_per_image, budget, seed=1, start=-1) -> list[int]:
+    """Configurations a searcher would measure, in order, on a table of known
+    times (host only; <= 0 marks an invalid configuration)."""
+    t = (ctypes.c_double * len(ns_per_image))(*[float(x) for x in ns_per_image])
+    out = (ctypes.c_int * max(1, budget))()
+    m = _lib().fr_search_simulate(int(search), t, len(ns_per_image), int(budget), int(seed),
+                                  int(start), out)
+    if m < 0:
+        raise FrError(-m, "fr_search_simulate")
+    return [out[k] for k in range(m)]
 
 
 def fr_prepare_images(ctx, real, out, center=False, n=None, stream=None):

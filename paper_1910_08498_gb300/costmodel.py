@@ -16,6 +16,10 @@ k = max(1, floor(N / 10)) evaluations (the tuner's default learned budget):
             expectation is computed exactly from the sorted times: the best
             of the draw is the i-th fastest with probability
             C(N-i, k-1) / C(N, k));
+  annealing, mcmc
+            the library's adaptive walks over neighbouring configurations,
+            simulated on the measured table (fr_search_simulate), mean over
+            20 seeds, started from the default configuration;
   regret = t(kept) / t(best of all N) - 1.
 
     python -m paper_1910_08498_gb300.costmodel --train sweep_train.json \
@@ -111,6 +115,33 @@ def evaluate(ctx, wl, frac=0.10):
     return out
 
 
+def compare_searchers(wl, frac=0.10, seeds=20, start=None, learned=None):
+    """Regret at equal budget k = max(1, floor(frac N)) of the random search
+    (exact expectation), simulated annealing and the Metropolis walk (mean
+    over `seeds` seeds, started from `start`, default: the library's default
+    configuration) and, if given, the learned ranking ({workload: regret})."""
+    ncfg = L.fr_num_configs()
+    if start is None:
+        start = 4  # gather 16 x 16 x 8, polynomial weights, 64 images per list
+    rows = []
+    for key, t in sorted(wl.items()):
+        table = [t.get(c, 0.0) for c in range(ncfg)]
+        k = max(1, int(frac * len(t) + 1e-9))
+        best = min(t.values())
+        row = {"S": key[0], "a": key[1], "n": key[2], "budget": k, "configs": len(t),
+               "random": random_expected_regret(list(t.values()), k)}
+        for name, search in (("annealing", L.FR_SEARCH_ANNEALING), ("mcmc", L.FR_SEARCH_MCMC)):
+            regs = []
+            for sd in range(seeds):
+                o = L.fr_search_simulate(search, table, k, seed=1000 + sd, start=start)
+                regs.append(min(table[c] for c in o) / best - 1.0)
+            row[name] = float(np.mean(regs))
+        if learned is not None and key in learned:
+            row["learned"] = learned[key]
+        rows.append(row)
+    return rows
+
+
 def summary(res):
     lr = np.array([r["learned_regret"] for r in res])
     rr = np.array([r["random_expected_regret"] for r in res])
@@ -138,11 +169,19 @@ def main(argv=None):
         res_in, res_out = evaluate(ctx, tr), evaluate(ctx, te)
         rep = {"final_loss": loss, "train": summary(res_in), "heldout": summary(res_out),
                "heldout_rows": res_out}
+        # the other searchers at the same budget (simulated on the measured tables)
+        learned = {(r["S"], r["a"], r["n"]): r["learned_regret"] for r in res_out}
+        cmp_rows = compare_searchers(te, learned=learned)
+        rep["searchers_heldout"] = {
+            name: {"mean_regret": float(np.mean([r[name] for r in cmp_rows])),
+                   "max_regret": float(np.max([r[name] for r in cmp_rows])),
+                   "within_5pct": float(np.mean([r[name] <= 0.05 for r in cmp_rows]))}
+            for name in ("random", "annealing", "mcmc", "learned")}
         if args.save:
             json.dump([float(x) for x in L.fr_mlp_get(ctx)], open(args.save, "w"))
     finally:
         L.fr_destroy(ctx)
-    print(json.dumps({k: v for k, v in rep.items() if k != "heldout_rows"}, indent=1))
+    print(json.dumps({k: v for k, v in rep.items() if k not in ("heldout_rows",)}, indent=1))
     if args.out:
         json.dump(rep, open(args.out, "w"), indent=1)
 

@@ -522,7 +522,7 @@ int fr_retune(fr_ctx *c, int all) {
 
 int fr_set_options(fr_ctx *c, const fr_options *o) {
   if (!c || !o) return FR_ERR_INVALID_ARG;
-  if (o->search < 0 || o->search > 2 || o->budget < 0 || o->steps_per_insert < 1)
+  if (o->search < 0 || o->search > FR_SEARCH_MCMC || o->budget < 0 || o->steps_per_insert < 1)
     return FR_ERR_INVALID_ARG;
   if (o->forced_config >= (int)config_space().size()) return FR_ERR_INVALID_ARG;
   if (o->forced_config >= 0 && !config_valid(c, o->forced_config)) return FR_ERR_UNSUPPORTED;

@@ -143,6 +143,14 @@ std::vector<int> Tuner::search_order(const TuneKey &k, fr_ctx *c) {
   std::mt19937_64 rng(o.seed ^ ((unsigned long long)k.S << 20) ^ ((unsigned long long)k.nb << 8) ^
                       (unsigned long long)k.dtype);
   std::vector<int> order = valid;
+  if (o.search == FR_SEARCH_ANNEALING || o.search == FR_SEARCH_MCMC) {
+    // adaptive: proposals are made step by step (plan); the order stays empty
+    KeyState &ks = keys_[k];
+    ks.adaptive = true;
+    ks.budget = o.budget > 0 ? o.budget : std::max(1, (int)(valid.size() / 10));
+    ks.walker.init(valid, default_config(c), o.search == FR_SEARCH_ANNEALING, rng());
+    return {};
+  }
   if (o.search == FR_SEARCH_LEARNED && c->mlp_trained) {
     int pb = -1;
     order = learned_order(c, k, valid, &pb);
@@ -180,6 +188,31 @@ std::vector<Step> Tuner::plan(KeyState &ks, int n, const fr_options &opt) {
   const int fallback = ks.best >= 0 ? ks.best : default_config(ctx_);
   if (!opt.tuning || ks.tuned) {
     steps.push_back(Step{fallback, n, false});
+    return steps;
+  }
+  if (ks.adaptive) {
+    // decide the proposals whose times are known, then propose this insert's steps
+    ks.walker.decide([&](int c) -> double {
+      if (ks.invalid.count(c)) return -1.0;
+      auto it = ks.meas.find(c);
+      return it == ks.meas.end() || it->second.images <= 0 ? 0.0 : it->second.per_image();
+    });
+    std::vector<int> cfgs;
+    const int k = std::min(std::min(opt.steps_per_insert, ks.budget - ks.proposed), n);
+    for (int i = 0; i < k; ++i) {
+      const int c = ks.walker.propose();
+      if (c < 0) break;
+      cfgs.push_back(c);
+    }
+    if (cfgs.empty()) {
+      ks.budget = ks.proposed;  // nothing left to propose
+      steps.push_back(Step{fallback, n, false});
+      return steps;
+    }
+    ks.proposed += (int)cfgs.size();
+    const int m = (int)cfgs.size();
+    const int base = n / m, extra = n % m;
+    for (int i = 0; i < m; ++i) steps.push_back(Step{cfgs[i], base + (i < extra ? 1 : 0), true});
     return steps;
   }
   // skip configurations found invalid
@@ -229,7 +262,8 @@ void Tuner::update_best(KeyState &ks) {
 }
 
 void Tuner::finish_if_done(KeyState &ks) {
-  if (!ks.tuned && ks.next >= ks.order.size() && ks.pending == 0) {
+  const bool exhausted = ks.adaptive ? ks.proposed >= ks.budget : ks.next >= ks.order.size();
+  if (!ks.tuned && exhausted && ks.pending == 0) {
     update_best(ks);
     ks.tuned = ks.best >= 0;
   }

@@ -21,18 +21,19 @@
 #include <string>
 #include <vector>
 
+#include "fr_search.h"
+
 struct fr_ctx;
 struct fr_options;
 struct fr_report;
-struct fr_ctx;
 
 namespace fr {
 
 struct Config {
   int algo;     // ALGO_GATHER or ALGO_SCATTER
   int shape;    // gather brick shape id
-  int wmode;    // W_LUT or W_OTF
-  int chunk;    // gather: images culled into the shared-memory list per CTA barrier
+  int wmode;    // W_LUT, W_OTF or W_POLY
+  int chunk;    // gather: capacity of a warp's shared-memory image list
   int threads;  // scatter: block size
   int sub;      // scatter: images per atomic sub-batch (merged after each)
 };
@@ -86,6 +87,11 @@ struct KeyState {
   double all_ns = 0, all_images = 0;  // every timed launch of this key
   int space_size = 0;
   int predicted_best = -1;            // learned search: the model's first choice
+  // adaptive searches (annealing, Metropolis): configurations are proposed
+  // one step at a time from the measurements known so far
+  bool adaptive = false;
+  int budget = 0, proposed = 0;
+  Walker walker;
 };
 
 struct Step {

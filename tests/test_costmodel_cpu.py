@@ -55,3 +55,43 @@ def test_shipped_model_and_sweeps_are_well_formed():
         assert d["space"] == [L.fr_describe_config(i) for i in range(L.fr_num_configs())]
         wl = cm.workloads(d["rows"])
         assert all(len(t) >= 10 and min(t.values()) > 0 for t in wl.values())
+
+
+def test_search_simulate_orders():
+    N = L.fr_num_configs()
+    rng = np.random.default_rng(5)
+    t = list(rng.uniform(1, 3, N))
+    t[7] = 0.0   # invalid
+    t[40] = -1.0  # invalid
+    valid = [c for c in range(N) if t[c] > 0]
+    assert L.fr_search_simulate(L.FR_SEARCH_EXHAUSTIVE, t, N) == valid
+    r = L.fr_search_simulate(L.FR_SEARCH_RANDOM, t, 10, seed=3)
+    assert len(r) == 10 and len(set(r)) == 10 and set(r) <= set(valid)
+    for s in (L.FR_SEARCH_ANNEALING, L.FR_SEARCH_MCMC):
+        o = L.fr_search_simulate(s, t, 12, seed=4, start=4)
+        assert o[0] == 4 and len(o) == 12 and len(set(o)) == 12 and set(o) <= set(valid)
+        full = L.fr_search_simulate(s, t, N, seed=4, start=4)
+        assert sorted(full) == valid          # a walk eventually proposes every valid one
+    with pytest.raises(L.FrError):
+        L.fr_search_simulate(L.FR_SEARCH_LEARNED, t, 4)
+
+
+def test_walks_beat_random_on_a_smooth_landscape():
+    """Time = 1 + (number of tuning dimensions that differ from a fixed
+    optimum): neighbours of the current configuration are one step closer or
+    farther, so the walks descend; random search does not use that."""
+    N = L.fr_num_configs()
+    desc = [L.fr_describe_config(c) for c in range(N)]
+    opt = desc.index("gather bx=32 by=8 zc=4 chunk=128 w=otf")
+
+    def dims(d):
+        return dict(x.split("=") for x in d.split()[1:]) | {"algo": d.split()[0]}
+
+    o = dims(desc[opt])
+    t = [1.0 + sum(dims(d).get(k) != v for k, v in o.items()) for d in desc]
+    wl = {(256, 1.9, 5000): {c: t[c] for c in range(N)}}
+    # the optimum is three improving moves from the start; with 19 evaluations
+    # the walks almost always reach it, random draws rarely do
+    rows = cm.compare_searchers(wl, frac=0.45, seeds=50, start=4)
+    assert rows[0]["annealing"] < 0.2 and rows[0]["mcmc"] < 0.2
+    assert rows[0]["random"] > 0.5

@@ -88,3 +88,26 @@ def test_tuning_with_every_search_keeps_results():
         finally:
             L.fr_destroy(ctx)
         assert rel_err(V, Vr) <= TOL_F32 and rel_err(W, Wr) <= TOL_F32
+
+
+@pytest.mark.parametrize("search", [L.FR_SEARCH_ANNEALING, L.FR_SEARCH_MCMC])
+def test_adaptive_walks_online(search):
+    """The adaptive searchers propose from harvested timings, stop at their
+    budget, settle on the fastest measured configuration and keep the
+    volume the oracle's."""
+    S = 40
+    batches = [inputs.make_batch(S, 120, 110 + b) for b in range(8)]
+    Vr, Wr, _ = oracle_insert(S, batches)
+    ctx = L.fr_create(S)
+    try:
+        L.fr_set_options(ctx, tuning=1, search=search, budget=7, steps_per_insert=2)
+        for img, rot in batches:
+            L.fr_insert(ctx, img.cuda(), rot.cuda())
+        rep = L.fr_tuning_report(ctx)
+        meas = L.fr_tuning_measurements(ctx)
+        V, W = _finalize(ctx, S)
+    finally:
+        L.fr_destroy(ctx)
+    assert rep["tuned"] == 1 and rep["evaluated"] == 7
+    assert rep["best_config"] == min(meas, key=lambda m: m[1])[0]
+    assert rel_err(V, Vr) <= TOL_F32 and rel_err(W, Wr) <= TOL_F32
