@@ -427,7 +427,7 @@ __device__ __noinline__ void box_careful(const InsertArgs &args, const float2 *l
 
 // Per-warp shared memory of the gather: image list, partial sums, item queues.
 __host__ __device__ constexpr size_t gather_warp_smem(int zc, int chunk) {
-  return (size_t)LIST_FIELDS * chunk * 4 + (size_t)3 * (32 * zc) * 4 + (size_t)4 * (32 * zc + 32) * 4;
+  return (size_t)LIST_FIELDS * chunk * 4 + (size_t)3 * (32 * zc) * 4 + (size_t)4 * (32 * zc + 32) * 2;
 }
 
 // Bytes of the InsertArgs copy at the head of each warp's shared memory in
@@ -453,14 +453,22 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
   static_assert(ZC <= 8, "item encoding holds 3 bits of z");
   const Geom &g = args.g;
   const int lane = threadIdx.x & 31;
-  const int lcap = args.chunk;  // list capacity per warp
+  const int lcap = args.chunk;  // list capacity per warp (<= 128: 7 bits of the item tags)
+  if (lcap > 128) {
+    if ((threadIdx.x & 31) == 0) set_err(args.err, DERR_RANGE);
+    return;
+  }
 
   float *s_list = reinterpret_cast<float *>(wsmem);      // [LIST_FIELDS][lcap]
   float *s_acc = s_list + (size_t)LIST_FIELDS * lcap;   // [3][WV]
-  unsigned *s_qf = reinterpret_cast<unsigned *>(s_acc + 3 * WV);  // fast items
-  unsigned *s_qe = s_qf + QCAP;                                    // fast items at the image edge
-  unsigned *s_qc = s_qe + QCAP;                                    // boxes crossing kx = 0
-  unsigned *s_qd = s_qc + QCAP;                                    // voxels in fold columns
+  // item queues of 16-bit tags li << 9 | mirrored << 8 | column << 3 | z level
+  // (list capacity <= 128): the less shared memory the warps take, the more
+  // of the SM's L1 is left for the pixel reads
+  using qtag = unsigned short;
+  qtag *s_qf = reinterpret_cast<qtag *>(s_acc + 3 * WV);  // fast items
+  qtag *s_qe = s_qf + QCAP;                              // fast items at the image edge
+  qtag *s_qc = s_qe + QCAP;                              // boxes crossing kx = 0
+  qtag *s_qd = s_qc + QCAP;                              // voxels in fold columns
   auto LF = [&](int f, int i) -> float & { return s_list[f * lcap + i]; };
   auto LI = [&](int f, int i) -> int { return __float_as_int(s_list[f * lcap + i]); };
 
@@ -595,7 +603,7 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
 
   // drain full rounds of 32 items (all of them if `all`); the remainder moves
   // to the front of the queue
-  auto drain = [&](unsigned *q, int &qlen, int kind, bool all) {
+  auto drain = [&](qtag *q, int &qlen, int kind, bool all) {
     __syncwarp();
     const long long t0 = tick();
     const int nfull = all ? qlen : (qlen & ~31);
@@ -609,7 +617,7 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
     __syncwarp();
     const int rest = qlen - nfull;
     if (rest) {
-      unsigned v = lane < rest ? q[nfull + lane] : 0u;
+      const qtag v = lane < rest ? q[nfull + lane] : (qtag)0;
       __syncwarp();
       if (lane < rest) q[lane] = v;
     }
@@ -668,7 +676,7 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
       const int p0 = qf + excl - t0;
 #pragma unroll
       for (int t = 0; t < ZC; ++t)
-        if ((near >> t) & 1u) s_qf[p0 + t] = base | (unsigned)t;
+        if ((near >> t) & 1u) s_qf[p0 + t] = (qtag)(base | (unsigned)t);
       qf += tot;
       return;
     } else {
@@ -710,17 +718,17 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
     while (mf) {
       const int t = __ffs(mf) - 1;
       mf &= mf - 1;
-      s_qf[pf++] = base | (((mneg >> t) & 1u) << 8) | (unsigned)t;
+      s_qf[pf++] = (qtag)(base | (((mneg >> t) & 1u) << 8) | (unsigned)t);
     }
     while (me) {
       const int t = __ffs(me) - 1;
       me &= me - 1;
-      s_qe[pe++] = base | (((mneg >> t) & 1u) << 8) | (unsigned)t;
+      s_qe[pe++] = (qtag)(base | (((mneg >> t) & 1u) << 8) | (unsigned)t);
     }
     while (mc) {
       const int t = __ffs(mc) - 1;
       mc &= mc - 1;
-      s_qc[pc++] = base | (unsigned)t;
+      s_qc[pc++] = (qtag)(base | (unsigned)t);
     }
     qf += total & 1023;
     qe += (total >> 10) & 1023;
@@ -738,7 +746,7 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
       while (md) {
         const int t = __ffs(md) - 1;
         md &= md - 1;
-        s_qd[pd++] = base | (unsigned)t;
+        s_qd[pd++] = (qtag)(base | (unsigned)t);
       }
       qd += __shfl_sync(0xffffffffu, incd, 31);
     }
