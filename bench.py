@@ -27,7 +27,9 @@ Phases (one JSON line at the end):
            learned search, with and without the tuning cache;
   batched  the uneven-batch workload (40 batches of S in {64..256}, n in
            [500, 5000]): one persistent-gather graph replay per pass against
-           one fr_insert per batch.
+           one fr_insert per batch;
+  gemm     the second dynamic-tuning workload (Sec. 5.2): batched small GEMM
+           with random size changes, tuned with the paper's stop rule.
 
 --impl reference times the FP64 CPU oracle (the definition, written as a
 plain scatter) on the host cores on a bounded sample of the same workload.
@@ -69,6 +71,8 @@ def parse():
     p.add_argument("--no-stream", action="store_true", help="skip the 20-batch stream with an S switch")
     p.add_argument("--no-fp16", action="store_true", help="skip the FP16-image measurement")
     p.add_argument("--no-recon", action="store_true", help="skip the reconstruction (last step) timing")
+    p.add_argument("--no-gemm", action="store_true", help="skip the batched-GEMM dynamic-tuning study")
+    p.add_argument("--only-gemm", action="store_true", help="run only the batched-GEMM study")
     p.add_argument("--only-batched", action="store_true",
                    help="profiling mode: run only the uneven-batch workload and print its result")
     p.add_argument("--seed", type=int, default=5)
@@ -506,6 +510,10 @@ def run_ours(args):
         stream_exp = run_stream(L, inputs, costmodel, dev, stream, batches, updates, n, f16,
                                 args.seed * 1000 + 500 + rank)
 
+    gemm_dyn = None
+    if not args.no_gemm:
+        gemm_dyn = run_gemm_dynamic(L, dev, stream)
+
     batched = None
     if not args.no_batched:
         batched = run_batched(L, inputs, dev, stream, max(2, args.steps // 3), 1, f16)
@@ -556,6 +564,7 @@ def run_ours(args):
         "prepare_images": prep,
         "stream": stream_exp,
         "batched": batched,
+        "gemm_dynamic": gemm_dyn,
         "gpu_launches": args.steps * launches_per_insert(L, best, n),
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
         "wall_s_timed": wall,
@@ -702,6 +711,73 @@ def run_stream(L, inputs, costmodel, dev, stream, batches256, updates256, n, f16
     return res
 
 
+def measured_hbm_gbs():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def run_gemm_dynamic(L, dev, stream, sizes=10, calls=100, seed=7, target_bytes=512e6):
+    """The dynamic-tuning study of Sec. 5.2 on the batched small GEMM: sizes
+    (m, n, k) drawn uniformly from [2, 32]^3 change every `calls` calls; the
+    tuner (random search, at most 20 configurations, stop at 75 % of the
+    measured HBM bandwidth) runs inside the calls.  Per size: Maximum = best
+    configuration measured offline (every valid one), Restricted = the
+    tuner's choice relative to it, Incl. overhead = all calls of the size
+    (tuning included) relative to it (the columns of the paper's Table 7)."""
+    import torch
+    peak, src = measured_hbm_gbs()
+    g = torch.Generator().manual_seed(seed)
+    ctx = L.fr_gemm_create()
+    L.fr_gemm_set_tuning(ctx, tuning=1, search=L.FR_SEARCH_RANDOM, budget=20, steps=2,
+                         bw_gbs=peak, bw_frac=0.75, seed=seed)
+    rows = []
+    try:
+        for _ in range(sizes):
+            m, n, k = (int(x) for x in torch.randint(2, 33, (3,), generator=g))
+            per = 4.0 * (m * k + k * n + m * n)
+            batch = int(min(1 << 26, max(1, target_bytes // per)))
+            A = torch.randn(batch, m, k, device=dev)
+            B = torch.randn(batch, k, n, device=dev)
+            C = torch.empty(batch, m, n, device=dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            best = 0.0
+            for cfg in range(L.fr_gemm_num_configs()):
+                if not L.fr_gemm_config_valid(cfg, m, n, k):
+                    continue
+                L.fr_gemm_run_config(cfg, A, B, C)
+                e0.record(stream)
+                for _ in range(3):
+                    L.fr_gemm_run_config(cfg, A, B, C)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                best = max(best, 3 * batch * per / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(calls):
+                L.fr_gemm_run(ctx, A, B, C)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            dyn = calls * batch * per / (e0.elapsed_time(e1) * 1e-3) / 1e9
+            rep = L.fr_gemm_report(ctx, m, n, k)
+            rows.append({"m": m, "n": n, "k": k, "batch": batch, "maximum_gbs": best,
+                         "restricted_pct": 100.0 * rep["best_gbs"] / best if best else None,
+                         "incl_overhead_pct": 100.0 * dyn / best if best else None,
+                         "evaluated": rep["evaluated"], "tuned": rep["tuned"],
+                         "config": L.fr_gemm_describe_config(rep["best"]) if rep["best"] >= 0 else None})
+            del A, B, C
+    finally:
+        L.fr_gemm_destroy(ctx)
+    import statistics as st
+    return {"sizes": rows, "calls_per_size": calls,
+            "maximum_gbs_avg": st.mean(r["maximum_gbs"] for r in rows),
+            "maximum_pct_of_hbm": 100.0 * st.mean(r["maximum_gbs"] for r in rows) / peak,
+            "restricted_pct_avg": st.mean(r["restricted_pct"] for r in rows),
+            "incl_overhead_pct_avg": st.mean(r["incl_overhead_pct"] for r in rows),
+            "hbm_gbs": peak, "hbm_source": src}
+
+
 def launches_per_insert(L, cfg, n):
     d = L.fr_describe_config(cfg)
     if d.startswith("gather"):
@@ -765,6 +841,14 @@ def main():
     args = parse()
     if args.profile_config is not None:
         return run_profile(args)
+    if args.only_gemm:
+        import torch
+
+        from paper_1910_08498_gb300 import _lib as L
+        L.lib()
+        print(json.dumps(run_gemm_dynamic(L, torch.device("cuda", 0), torch.cuda.current_stream())),
+              flush=True)
+        return 0
     if args.only_batched:
         import torch
 

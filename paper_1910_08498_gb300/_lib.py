@@ -126,6 +126,15 @@ def _lib():
             "fr_reconstruct": (i, [vp, vp, f, vp]),
             "fr_prepare_images": (i, [vp, vp, i, i, vp, i, vp]),
             "fr_search_simulate": (i, [i, P(d), i, i, ctypes.c_uint64, i, P(i)]),
+            "fr_gemm_create": (i, [P(vp)]),
+            "fr_gemm_destroy": (i, [vp]),
+            "fr_gemm_set_tuning": (i, [vp, i, i, i, i, d, d, ctypes.c_uint64]),
+            "fr_gemm_run": (i, [vp, i, i, i, vp, vp, vp, i, vp]),
+            "fr_gemm_run_config": (i, [i, i, i, i, vp, vp, vp, i, vp]),
+            "fr_gemm_num_configs": (i, []),
+            "fr_gemm_describe_config": (i, [i, ctypes.c_char_p, i]),
+            "fr_gemm_config_valid": (i, [i, i, i, i]),
+            "fr_gemm_report": (i, [vp, i, i, i, P(i), P(i), P(i), P(d), P(d)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -420,3 +429,67 @@ def fr_mlp_set(ctx, params):
     assert p.size == MLP_NPARAM
     return _check(_lib().fr_mlp_set(ctx, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
                   "fr_mlp_set")
+
+
+# ---------------------------------------------------------------- batched GEMM (fr_gemm.h)
+
+def fr_gemm_create():
+    h = ctypes.c_void_p()
+    _check(_lib().fr_gemm_create(ctypes.byref(h)), "fr_gemm_create")
+    return h
+
+
+def fr_gemm_destroy(ctx):
+    return _check(_lib().fr_gemm_destroy(ctx), "fr_gemm_destroy")
+
+
+def fr_gemm_set_tuning(ctx, tuning=1, search=FR_SEARCH_RANDOM, budget=20, steps=2, bw_gbs=0.0,
+                       bw_frac=0.75, seed=1):
+    return _check(_lib().fr_gemm_set_tuning(ctx, int(tuning), int(search), int(budget), int(steps),
+                                            float(bw_gbs), float(bw_frac), int(seed)),
+                  "fr_gemm_set_tuning")
+
+
+def _gemm_args(A, B, C):
+    batch, m, k = A.shape
+    assert B.shape[0] == batch and B.shape[1] == k and C.shape == (batch, m, B.shape[2])
+    for t in (A, B, C):
+        assert t.is_cuda and t.is_contiguous()
+    return m, B.shape[2], k, batch
+
+
+def fr_gemm_run(ctx, A, B, C, stream=None):
+    """C[b] = A[b] B[b] (CUDA float32 [batch, m, k] x [batch, k, n]), tuned dynamically."""
+    m, n, k, batch = _gemm_args(A, B, C)
+    return _check(_lib().fr_gemm_run(ctx, m, n, k, _ptr(A), _ptr(B), _ptr(C), batch, _stream(stream)),
+                  "fr_gemm_run")
+
+
+def fr_gemm_run_config(config, A, B, C, stream=None):
+    m, n, k, batch = _gemm_args(A, B, C)
+    return _check(_lib().fr_gemm_run_config(int(config), m, n, k, _ptr(A), _ptr(B), _ptr(C), batch,
+                                            _stream(stream)), "fr_gemm_run_config")
+
+
+def fr_gemm_num_configs() -> int:
+    return _lib().fr_gemm_num_configs()
+
+
+def fr_gemm_describe_config(i: int) -> str:
+    buf = ctypes.create_string_buffer(64)
+    _check(_lib().fr_gemm_describe_config(i, buf, 64), "fr_gemm_describe_config")
+    return buf.value.decode()
+
+
+def fr_gemm_config_valid(i, m, n, k) -> bool:
+    return bool(_lib().fr_gemm_config_valid(int(i), int(m), int(n), int(k)))
+
+
+def fr_gemm_report(ctx, m, n, k) -> dict:
+    t, e, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    g, o = ctypes.c_double(), ctypes.c_double()
+    _check(_lib().fr_gemm_report(ctx, m, n, k, ctypes.byref(t), ctypes.byref(e), ctypes.byref(b),
+                                 ctypes.byref(g), ctypes.byref(o)), "fr_gemm_report")
+    return {"tuned": t.value, "evaluated": e.value, "best": b.value, "best_gbs": g.value,
+            "overhead_pct": o.value}
+
