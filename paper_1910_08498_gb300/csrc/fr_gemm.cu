@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <map>
 #include <mutex>
@@ -59,6 +60,25 @@ bool gemm_valid(int id, int m, int n, int k) {
   return t >= 32 && t <= 1024 && gemm_smem(c, m, n, k) <= 48 * 1024;
 }
 
+// dst[i] = src[i] for i < count (src in global memory): 16-byte loads over the
+// 16-byte aligned middle, scalar loads for the ends
+__device__ __forceinline__ void copy_to_smem(float *dst, const float *src, int count) {
+  const int head = (int)(((16 - (reinterpret_cast<uintptr_t>(src) & 15)) & 15) >> 2);
+  const int h = min(head, count);
+  for (int i = threadIdx.x; i < h; i += blockDim.x) dst[i] = __ldg(src + i);
+  const int nv = (count - h) >> 2;
+  const float4 *s4 = reinterpret_cast<const float4 *>(src + h);
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    const float4 x = __ldg(s4 + v);
+    float *d = dst + h + 4 * v;
+    d[0] = x.x;
+    d[1] = x.y;
+    d[2] = x.z;
+    d[3] = x.w;
+  }
+  for (int i = h + 4 * nv + threadIdx.x; i < count; i += blockDim.x) dst[i] = __ldg(src + i);
+}
+
 template <int Y, int STAGE>
 __global__ void bgemm_kernel(int m, int n, int k, int z, const float *__restrict__ A,
                              const float *__restrict__ B, float *__restrict__ C, int batch) {
@@ -70,8 +90,8 @@ __global__ void bgemm_kernel(int m, int n, int k, int z, const float *__restrict
   const int T = blockDim.x;
   const float *gA = A + b0 * mk;
   const float *gB = B + b0 * kn;
-  for (int i = threadIdx.x; i < nb * mk; i += T) sA[i] = __ldg(gA + i);
-  for (int i = threadIdx.x; i < nb * kn; i += T) sB[i] = __ldg(gB + i);
+  copy_to_smem(sA, gA, nb * mk);
+  copy_to_smem(sB, gB, nb * kn);
   __syncthreads();
   const int my = (m + Y - 1) / Y;
   const int j = threadIdx.x % n, t = threadIdx.x / n;
