@@ -3,6 +3,8 @@
 // test hooks for the fold predicate and the blob weights.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "fr_device.cuh"
 #include "fr_internal.h"
 
@@ -146,54 +148,69 @@ __global__ void finalize_kernel(const Geom g, const float *__restrict__ acc, siz
 // boundary are re-decided exactly as the FP64 definition states (products of
 // an FP32 entry and an integer are exact in FP64), so the count equals the
 // definition's.  This is a measurement helper, not part of the insertion.
+// Exact number of (pixel, voxel) updates of a batch (the metric's unit).
+// Images along grid y, pixels along grid x (32-bit index arithmetic); a row
+// of candidates whose own distance already exceeds a is skipped; r <= a is
+// decided in FP32 away from the edge and, within 1e-5 a^2 of it, with the
+// definition's own FP64 operations.
 __global__ void count_kernel(const Geom g, const float *rot, int n, unsigned long long *out) {
   const float a = g.a, a2 = g.a2;
+  const float a2_row = a2 * (1.0f + 1e-4f);
   const double a2d = (double)g.a * (double)g.a;
+  const int npx = g.S * g.NX;
+  const int span = (int)floorf(2.f * a) + 3;
   unsigned long long cnt = 0;
-  const size_t total = (size_t)n * g.S * g.NX;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int kx = (int)(idx % g.NX);
-    const size_t r = idx / g.NX;
-    const int row = (int)(r % g.S);
-    const int i = (int)(r / g.S);
-    const int ky = row < g.H ? row : row - g.S;
+  for (int i = blockIdx.y; i < n; i += gridDim.y) {
     const float *R = rot + 9 * (size_t)i;
     float Rv[6] = {__ldg(R + 0), __ldg(R + 1), __ldg(R + 3), __ldg(R + 4), __ldg(R + 6),
                    __ldg(R + 7)};
-    float qh[3], ql[3];
-    for (int c = 0; c < 3; ++c) rk_dd(Rv[2 * c], Rv[2 * c + 1], (float)kx, (float)ky, qh[c], ql[c]);
-    float sg = 1.f;
-    if (fold_pred(Rv[0], Rv[1], kx, ky)) sg = -1.f;
-    for (int c = 0; c < 3; ++c) { qh[c] *= sg; ql[c] *= sg; }
-    const int lo0 = (int)ceilf((qh[0] + ql[0]) - a) - 1, lo1 = (int)ceilf((qh[1] + ql[1]) - a) - 1,
-              lo2 = (int)ceilf((qh[2] + ql[2]) - a) - 1;
-    const int span = (int)floorf(2.f * a) + 3;
-    for (int z = lo2; z < lo2 + span; ++z) {
-      if (z < -g.H || z > g.H) continue;
-      for (int y = lo1; y < lo1 + span; ++y) {
-        if (y < -g.H || y > g.H) continue;
-        for (int x = lo0; x < lo0 + span; ++x) {
-          if (x < -g.H || x > g.H) continue;
-          float fx = ((float)x - qh[0]) - ql[0], fy = ((float)y - qh[1]) - ql[1],
-                fz = ((float)z - qh[2]) - ql[2];
-          float r2 = fx * fx + fy * fy + fz * fz;
-          bool in;
-          if (fabsf(r2 - a2) > 1e-3f) {
-            in = r2 <= a2;
-          } else {
-            // same operations and order as the definition, no contraction
-            double s = (double)sg;
-            double qx = s * __dadd_rn((double)Rv[0] * kx, (double)Rv[1] * ky);
-            double qy = s * __dadd_rn((double)Rv[2] * kx, (double)Rv[3] * ky);
-            double qz = s * __dadd_rn((double)Rv[4] * kx, (double)Rv[5] * ky);
-            double dx = x - qx, dy = y - qy, dz = z - qz;
-            double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-            in = d2 <= a2d;
+    for (int px = blockIdx.x * blockDim.x + threadIdx.x; px < npx; px += gridDim.x * blockDim.x) {
+      const int row = px / g.NX;
+      const int kx = px - row * g.NX;
+      const int ky = row < g.H ? row : row - g.S;
+      float qh[3], ql[3];
+      for (int c = 0; c < 3; ++c) rk_dd(Rv[2 * c], Rv[2 * c + 1], (float)kx, (float)ky, qh[c], ql[c]);
+      float sg = 1.f;
+      if (fold_pred(Rv[0], Rv[1], kx, ky)) sg = -1.f;
+      for (int c = 0; c < 3; ++c) { qh[c] *= sg; ql[c] *= sg; }
+      const int lo0 = (int)ceilf((qh[0] + ql[0]) - a) - 1, lo1 = (int)ceilf((qh[1] + ql[1]) - a) - 1,
+                lo2 = (int)ceilf((qh[2] + ql[2]) - a) - 1;
+      unsigned c32 = 0;
+      for (int z = lo2; z < lo2 + span; ++z) {
+        if (z < -g.H || z > g.H) continue;
+        const float fz = ((float)z - qh[2]) - ql[2];
+        const float rz = fz * fz;
+        if (rz > a2_row) continue;
+        for (int y = lo1; y < lo1 + span; ++y) {
+          if (y < -g.H || y > g.H) continue;
+          const float fy = ((float)y - qh[1]) - ql[1];
+          const float ryz = fy * fy + rz;
+          if (ryz > a2_row) continue;
+          for (int x = lo0; x < lo0 + span; ++x) {
+            if (x < -g.H || x > g.H) continue;
+            const float fx = ((float)x - qh[0]) - ql[0];
+            const float r2 = fx * fx + ryz;
+            bool in;
+            // FP32 r^2 is within a few 1e-6 of the exact value (q kept as a
+            // double-float pair): outside a band of 1e-5 a^2 it decides,
+            // inside it the definition's FP64 evaluation does
+            if (fabsf(r2 - a2) > 1e-5f * a2) {
+              in = r2 <= a2;
+            } else {
+              // same operations and order as the definition, no contraction
+              double s = (double)sg;
+              double qx = s * __dadd_rn((double)Rv[0] * kx, (double)Rv[1] * ky);
+              double qy = s * __dadd_rn((double)Rv[2] * kx, (double)Rv[3] * ky);
+              double qz = s * __dadd_rn((double)Rv[4] * kx, (double)Rv[5] * ky);
+              double dx = x - qx, dy = y - qy, dz = z - qz;
+              double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+              in = d2 <= a2d;
+            }
+            c32 += in;
           }
-          cnt += in;
         }
       }
+      cnt += c32;
     }
   }
   // warp reduce, one atomic per warp
@@ -289,9 +306,12 @@ cudaError_t launch_finalize(const Geom &g, const float *acc, size_t plane, float
 
 cudaError_t launch_count(const Geom &g, const float *rot, int n, unsigned long long *out,
                          cudaStream_t st) {
-  size_t total = (size_t)n * g.S * g.NX;
-  int threads = 256;
-  count_kernel<<<grid_for(total, threads, sm_count() * 8), threads, 0, st>>>(g, rot, n, out);
+  if (n <= 0) return cudaSuccess;
+  const int threads = 256;
+  const int npx = g.S * g.NX;
+  const int bx = std::max(1, std::min((npx + threads - 1) / threads, 64));
+  const int by = std::max(1, std::min(n, (sm_count() * 8 + bx - 1) / bx * 4));
+  count_kernel<<<dim3(bx, std::min(by, 65535)), threads, 0, st>>>(g, rot, n, out);
   return cudaGetLastError();
 }
 
