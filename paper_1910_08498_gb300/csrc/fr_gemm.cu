@@ -2,12 +2,14 @@
 // the non-blocking dynamic tuning of Sec. 3.2 under matrix-size changes
 // (Sec. 5.2); the C ABI of include/fr_gemm.h.
 //
-// Kernel: a CTA computes Z consecutive instances.  It copies their A and B
+// Kernels: a CTA computes Z consecutive instances.  It copies their A and B
 // blocks (contiguous in memory) into shared memory with coalesced loads;
 // thread (j, ty, tz) then computes column j of rows ty*Y .. ty*Y+Y-1 of
 // instance tz, with a sequential FMA over the inner dimension.  With STAGE,
 // the CTA's C block is assembled in shared memory and written back with
-// coalesced stores; otherwise each thread stores its Y values directly.
+// coalesced stores; otherwise each thread stores its Y values directly.  The
+// pipelined variant keeps a grid of resident CTAs that prefetch their next
+// group of instances with cp.async while computing the current one.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,15 +33,17 @@ namespace fr {
 namespace {
 
 struct GemmConfig {
-  int y, z, stage;
+  int y, z, stage, pipe;  // pipe: persistent CTAs, next group prefetched with cp.async
 };
 
 const std::vector<GemmConfig> &gemm_space() {
   static const std::vector<GemmConfig> v = [] {
     std::vector<GemmConfig> c;
     for (int y : {1, 2, 4, 8})
-      for (int z : {1, 2, 4, 8, 16, 32})
-        for (int st : {0, 1}) c.push_back(GemmConfig{y, z, st});
+      for (int z : {1, 2, 4, 8, 16, 32}) {
+        for (int st : {0, 1}) c.push_back(GemmConfig{y, z, st, 0});
+        c.push_back(GemmConfig{y, z, 0, 1});
+      }
     return c;
   }();
   return v;
@@ -48,6 +52,8 @@ const std::vector<GemmConfig> &gemm_space() {
 int gemm_threads(const GemmConfig &c, int m, int n) { return n * ((m + c.y - 1) / c.y) * c.z; }
 
 size_t gemm_smem(const GemmConfig &c, int m, int n, int k) {
+  if (c.pipe)  // two buffers of A and B, each with 16 B of alignment slack
+    return 2 * ((size_t)c.z * ((size_t)m * k + (size_t)k * n) * sizeof(float) + 32);
   return (size_t)c.z * ((size_t)m * k + (size_t)k * n + (c.stage ? (size_t)m * n : 0)) * sizeof(float);
 }
 
@@ -126,6 +132,94 @@ __global__ void bgemm_kernel(int m, int n, int k, int z, const float *__restrict
   }
 }
 
+// Asynchronous copy of count floats from global src to shared dst, where
+// dst and src have the same address modulo 16: 16-byte copies over the
+// aligned middle, 4-byte copies at the ends.
+__device__ __forceinline__ void async_copy(float *dst, const float *src, int count) {
+  const int head = (int)(((16 - (reinterpret_cast<uintptr_t>(src) & 15)) & 15) >> 2);
+  const int h = min(head, count);
+  const uint32_t d0 = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+  for (int i = threadIdx.x; i < h; i += blockDim.x)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d0 + 4 * i), "l"(src + i) : "memory");
+  const int nv = (count - h) >> 2;
+  for (int v = threadIdx.x; v < nv; v += blockDim.x)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d0 + 4 * (h + 4 * v)),
+                 "l"(src + h + 4 * v)
+                 : "memory");
+  for (int i = h + 4 * nv + threadIdx.x; i < count; i += blockDim.x)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d0 + 4 * i), "l"(src + i) : "memory");
+}
+
+// Persistent variant: CTA c computes the groups c, c + gridDim.x, ... of z
+// instances; while it computes one group, the next one's A and B are copied
+// into the other shared-memory buffer (two-stage pipeline, cp.async).
+template <int Y>
+__global__ void bgemm_pipe_kernel(int m, int n, int k, int z, const float *__restrict__ A,
+                                  const float *__restrict__ B, float *__restrict__ C, int batch) {
+  extern __shared__ __align__(16) float sm[];
+  const int mk = m * k, kn = k * n, mn = m * n;
+  const int buf_floats = z * (mk + kn) + 8;  // + slack to match the source alignment
+  const long long groups = ((long long)batch + z - 1) / z;
+  const int my = (m + Y - 1) / Y;
+  const int j = threadIdx.x % n, t = threadIdx.x / n;
+  const int ty = t % my, tz = t / my;
+  // p moved up by 0..3 floats to the same address modulo 16 as src
+  auto align_like = [](float *p, const float *src) -> float * {
+    const uintptr_t d = (reinterpret_cast<uintptr_t>(src) - reinterpret_cast<uintptr_t>(p)) & 15;
+    return p + (d >> 2);
+  };
+  // where group g's A and B land in buffer s
+  auto bases = [&](long long g, int s, float *&sA, float *&sB) {
+    sA = align_like(sm + s * buf_floats, A + g * z * mk);
+    sB = align_like(sA + z * mk, B + g * z * kn);
+  };
+  auto issue = [&](long long g, int s) {
+    const long long b0 = g * z;
+    const int nb = (int)min((long long)z, batch - b0);
+    float *sA, *sB;
+    bases(g, s, sA, sB);
+    async_copy(sA, A + b0 * mk, nb * mk);
+    async_copy(sB, B + b0 * kn, nb * kn);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  long long g = blockIdx.x;
+  int s = 0;
+  if (g < groups) issue(g, 0);
+  for (; g < groups; g += gridDim.x, s ^= 1) {
+    const long long gn = g + gridDim.x;
+    if (gn < groups) {
+      issue(gn, s ^ 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    const long long b0 = g * z;
+    const int nb = (int)min((long long)z, batch - b0);
+    float *sA, *sB;
+    bases(g, s, sA, sB);
+    if (tz < nb) {
+      float acc[Y];
+#pragma unroll
+      for (int r = 0; r < Y; ++r) acc[r] = 0.f;
+      const float *a = sA + tz * mk + ty * Y * k;
+      const float *bb = sB + tz * kn + j;
+      for (int p = 0; p < k; ++p) {
+        const float bv = bb[p * n];
+#pragma unroll
+        for (int r = 0; r < Y; ++r)
+          if (ty * Y + r < m) acc[r] = fmaf(a[r * k + p], bv, acc[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < Y; ++r) {
+        const int row = ty * Y + r;
+        if (row < m) C[(b0 + tz) * mn + row * n + j] = acc[r];
+      }
+    }
+    __syncthreads();  // buffer s is refilled two groups later
+  }
+}
+
 template <int Y, int STAGE>
 cudaError_t launch_t(const GemmConfig &c, int m, int n, int k, const float *A, const float *B,
                      float *C, int batch, cudaStream_t st) {
@@ -137,10 +231,36 @@ cudaError_t launch_t(const GemmConfig &c, int m, int n, int k, const float *A, c
   return cudaGetLastError();
 }
 
+template <int Y>
+cudaError_t launch_pipe(const GemmConfig &c, int m, int n, int k, const float *A, const float *B,
+                        float *C, int batch, cudaStream_t st) {
+  const int threads = gemm_threads(c, m, n);
+  const size_t smem = gemm_smem(c, m, n, k);
+  auto fn = bgemm_pipe_kernel<Y>;
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+  if (e != cudaSuccess) return e;
+  const long long groups = ((long long)batch + c.z - 1) / c.z;
+  const long long grid = std::min<long long>(groups, (long long)std::max(per_sm, 1) * sms);
+  fn<<<(unsigned)grid, threads, smem, st>>>(m, n, k, c.z, A, B, C, batch);
+  return cudaGetLastError();
+}
+
 cudaError_t gemm_launch(int id, int m, int n, int k, const float *A, const float *B, float *C,
                         int batch, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
   const GemmConfig &c = gemm_space()[id];
+  if (c.pipe) {
+    switch (c.y) {
+      case 1: return launch_pipe<1>(c, m, n, k, A, B, C, batch, st);
+      case 2: return launch_pipe<2>(c, m, n, k, A, B, C, batch, st);
+      case 4: return launch_pipe<4>(c, m, n, k, A, B, C, batch, st);
+      case 8: return launch_pipe<8>(c, m, n, k, A, B, C, batch, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (c.y * 2 + c.stage) {
     case 2: return launch_t<1, 0>(c, m, n, k, A, B, C, batch, st);
     case 3: return launch_t<1, 1>(c, m, n, k, A, B, C, batch, st);
@@ -274,7 +394,8 @@ struct fr_gemm_ctx {
       for (int a : valid)
         for (int b : valid) {
           const GemmConfig &x = gemm_space()[a], &y = gemm_space()[b];
-          if ((x.y != y.y) + (x.z != y.z) + (x.stage != y.stage) == 1) ks.walker.nbr[a].push_back(b);
+          if ((x.y != y.y) + (x.z != y.z) + (x.stage != y.stage) + (x.pipe != y.pipe) == 1)
+            ks.walker.nbr[a].push_back(b);
         }
       ks.walker.anneal = search == FR_SEARCH_ANNEALING;
       ks.walker.T = ks.walker.anneal ? 0.2 : 0.1;
@@ -336,7 +457,8 @@ int fr_gemm_num_configs(void) { return (int)gemm_space().size(); }
 int fr_gemm_describe_config(int id, char *buf, int len) {
   if (id < 0 || id >= (int)gemm_space().size() || !buf || len < 1) return FR_ERR_INVALID_ARG;
   const GemmConfig &c = gemm_space()[id];
-  std::snprintf(buf, len, "bgemm y=%d z=%d stage=%d", c.y, c.z, c.stage);
+  std::snprintf(buf, len, "bgemm y=%d z=%d %s", c.y, c.z,
+                c.pipe ? "pipelined" : (c.stage ? "stage=1" : "stage=0"));
   return FR_OK;
 }
 
