@@ -74,3 +74,38 @@ def test_full_size_sampled_voxels(batch, samples, cfg):
     ew = np.abs(Wg - Wo) / scale_w
     assert ev.max() <= TOL_F32, (cfg, ev.max(), pts[int(ev.argmax())])
     assert ew.max() <= TOL_F32, (cfg, ew.max(), pts[int(ew.argmax())])
+
+
+@pytest.mark.parametrize("cfg", [-1, 41])
+def test_largest_image_size_sampled_voxels(cfg):
+    """S = 512, the largest size the library accepts (default gather and a
+    scatter configuration), on sampled voxels computed one by one."""
+    S2, n2 = 512, 120
+    img, rot = inputs.make_batch(S2, n2, 512)
+    H = S2 // 2
+    rng = np.random.default_rng(12)
+    pts = [(0, 0, 0), (1, 0, 0), (H, H, H), (-1, -H, H), (200, -100, 50)]
+    pts += [tuple(int(v) for v in rng.integers(-4, 5, 3)) for _ in range(6)]
+    pts += [(int(rng.integers(-1, H + 1)), int(rng.integers(-H, H + 1)), int(rng.integers(-H, H + 1)))
+            for _ in range(9)]
+    Vo, Wo = oracle.voxels(S2, img.numpy(), rot.numpy(), pts, a=A32, alpha=ALPHA)
+    ctx = L.fr_create(S2, A32, ALPHA, 0, 10000)
+    try:
+        if cfg >= 0 and not L.fr_config_valid(ctx, cfg):
+            pytest.skip("configuration not valid here")
+        L.fr_set_options(ctx, tuning=0, forced_config=cfg)
+        L.fr_insert(ctx, img.cuda(), rot.cuda())
+        D = S2 + 1
+        V = torch.empty(D ** 3, dtype=torch.complex64, device="cuda")
+        W = torch.empty(D ** 3, dtype=torch.float32, device="cuda")
+        L.fr_finalize(ctx, V, W)
+        torch.cuda.synchronize()
+        assert L.fr_last_device_error(ctx) == L.FR_OK
+        scale_v, scale_w = V.abs().max().item(), W.max().item()
+        idx = torch.tensor([((z + H) * D + (y + H)) * D + (x + H) for x, y, z in pts]).cuda()
+        Vg = V[idx].cpu().numpy().astype(np.complex128)
+        Wg = W[idx].cpu().numpy().astype(np.float64)
+    finally:
+        L.fr_destroy(ctx)
+    assert np.max(np.abs(Vg - Vo)) <= TOL_F32 * scale_v
+    assert np.max(np.abs(Wg - Wo)) <= TOL_F32 * scale_w

@@ -207,3 +207,36 @@ def test_tuning_steps_keep_every_image_once():
     assert rel_err(V, Vr) <= TOL_F32 and rel_err(W, Wr) <= TOL_F32
     assert rep["evaluated"] >= 20
     assert rep["images"] == 720
+
+
+def test_largest_blob_radius():
+    """a just below 3 (the largest radius accepted; 6 x 6 candidate boxes with
+    no spare cell) on every weight variant of the default shape and a scatter
+    configuration."""
+    S = 40
+    a = float(np.float32(2.99))
+    img, rot = inputs.make_batch(S, 50, 17)
+    Vr, Wr, _ = oracle_insert(S, [(img, rot)], a=a, alpha=ALPHA)
+    for cfg in (-1, 3, 4, 5, 41):
+        V, W, _ = gpu_insert(S, [(img, rot)], a=a, alpha=ALPHA, config=cfg, tuning=False)
+        assert rel_err(V, Vr) <= TOL_F32, (cfg, rel_err(V, Vr), worst(V, Vr, S))
+        assert rel_err(W, Wr) <= TOL_F32, (cfg, rel_err(W, Wr), worst(W, Wr, S))
+
+
+def test_invalid_arguments_leave_the_volume_untouched():
+    S = 16
+    img, rot = inputs.make_batch(S, 4, 18)
+    ctx = L.fr_create(S)
+    try:
+        lib = L.lib()
+        assert lib.fr_insert(ctx, L._ptr(img.cuda()), 7, L._ptr(rot.cuda()), 4, None) == L.FR_ERR_INVALID_ARG
+        assert lib.fr_insert(ctx, None, 0, None, 4, None) == L.FR_ERR_INVALID_ARG
+        assert lib.fr_insert(ctx, L._ptr(img.cuda()), 0, L._ptr(rot.cuda()), -1, None) == L.FR_ERR_INVALID_ARG
+        D = S + 1
+        V = torch.ones(D ** 3, dtype=torch.complex64, device="cuda")
+        W = torch.ones(D ** 3, dtype=torch.float32, device="cuda")
+        L.fr_finalize(ctx, V, W)
+        torch.cuda.synchronize()
+        assert torch.count_nonzero(W).item() == 0
+    finally:
+        L.fr_destroy(ctx)
