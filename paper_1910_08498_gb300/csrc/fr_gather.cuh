@@ -347,12 +347,14 @@ __device__ __forceinline__ void box_poly_fold(const InsertArgs &args, const floa
       const float pv = poly_eo(c, fmaf(r2, two_inv_a2, -1.0f));
       pixel(j, l, (r2 <= a2 && !tie) ? pv : 0.f);
     }
-    // the kx = 0 column's second pixel (0, -cy)
-    const bool dc0 = cy == 0;
-    const float r2 = dc0 ? vr2 : fmaf(dx0, dx0, ry);
-    const bool tie0 = !dc0 && fabsf(r2 - a2) <= tie_band;
-    const float pv = poly_eo(c, fmaf(r2, two_inv_a2, -1.0f));
-    column0(l, (has0 && r2 <= a2 && !tie0) ? pv : 0.f);
+    // the kx = 0 column's second pixel (0, -cy), when the box holds that column
+    if (has0) {
+      const bool dc0 = cy == 0;
+      const float r2 = dc0 ? vr2 : fmaf(dx0, dx0, ry);
+      const bool tie0 = !dc0 && fabsf(r2 - a2) <= tie_band;
+      const float pv = poly_eo(c, fmaf(r2, two_inv_a2, -1.0f));
+      column0(l, (r2 <= a2 && !tie0) ? pv : 0.f);
+    }
   }
   // candidates within rounding of the blob edge: decide as the real numbers do
   while (ties) {
