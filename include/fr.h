@@ -102,7 +102,10 @@ typedef struct fr_options {
     uint64_t seed;       /* seed of the search order (default 1) */
     int debug;           /* bit 0: synchronise after every launch and check the device error
                             word; bit 1: collect gather phase counters */
-    int reserved[8];
+    int fault_config;    /* test hook (host-side fault injection): > 0 makes every launch of
+                            configuration fault_config - 1 report a launch failure without
+                            enqueuing work, so the fallback path runs; 0 (default): none */
+    int reserved[7];
 } fr_options;
 
 /* What the tuner has done for the context's current key. */
@@ -170,6 +173,17 @@ int fr_insert(fr_ctx *ctx, const void *images, fr_dtype dtype, const float *rota
 int fr_insert_batched(fr_ctx *const *ctxs, const void *const *images, const fr_dtype *dtypes,
                       const float *const *rotations, const int *n, int nb, int capture,
                       void *stream);
+
+/* Checkpoint of the accumulated volume: the context's six accumulator planes
+ * (hi and lo of V.re, V.im, W; fr_state_bytes bytes).  fr_state_save copies
+ * them to dst, fr_state_load replaces them with src (host or device memory,
+ * any alignment), so that a context of the same S and blob resumes where the
+ * saved one stopped: later inserts add to the loaded sums exactly as they
+ * would have to the original ones.  Both wait for the context's queued work.
+ * Tuning state is saved separately (fr_tuning_save). */
+size_t fr_state_bytes(const fr_ctx *ctx);
+int fr_state_save(fr_ctx *ctx, void *dst);
+int fr_state_load(fr_ctx *ctx, const void *src);
 
 /* Write the accumulated volume: V (device, complex64 (S+1)^3) and W (device,
  * float32 (S+1)^3), [z][y][x].  Raw sums: no normalisation and no Hermitian

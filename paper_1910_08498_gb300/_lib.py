@@ -43,8 +43,8 @@ class fr_blob(ctypes.Structure):
 class fr_options(ctypes.Structure):
     _fields_ = [("tuning", ctypes.c_int), ("search", ctypes.c_int), ("budget", ctypes.c_int),
                 ("steps_per_insert", ctypes.c_int), ("forced_config", ctypes.c_int),
-                ("seed", ctypes.c_uint64), ("debug", ctypes.c_int),
-                ("reserved", ctypes.c_int * 8)]
+                ("seed", ctypes.c_uint64), ("debug", ctypes.c_int), ("fault_config", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
 
 
 class fr_report(ctypes.Structure):
@@ -124,6 +124,9 @@ def _lib():
             "fr_mlp_set": (i, [vp, P(f)]),
             "fr_insert_noalloc": (i, [i, f, f, vp, i, vp, i, vp, vp, vp]),
             "fr_reconstruct": (i, [vp, vp, f, vp]),
+            "fr_state_bytes": (ctypes.c_size_t, [vp]),
+            "fr_state_save": (i, [vp, vp]),
+            "fr_state_load": (i, [vp, vp]),
             "fr_prepare_images": (i, [vp, vp, i, i, vp, i, vp]),
             "fr_search_simulate": (i, [i, P(d), i, i, ctypes.c_uint64, i, P(i)]),
             "fr_gemm_create": (i, [P(vp)]),
@@ -238,6 +241,22 @@ def fr_prepare_images(ctx, real, out, center=False, n=None, stream=None):
     assert real.is_cuda and out.is_cuda and real.is_contiguous() and out.is_contiguous()
     return _check(_lib().fr_prepare_images(ctx, _ptr(real), int(n), int(bool(center)), _ptr(out),
                                            _dtype_of(out), _stream(stream)), "fr_prepare_images")
+
+
+def fr_state_bytes(ctx) -> int:
+    return int(_lib().fr_state_bytes(ctx))
+
+
+def fr_state_save(ctx, dst):
+    """Copy the accumulator planes into dst (a torch tensor on the host or the
+    device with at least fr_state_bytes bytes)."""
+    assert dst.is_contiguous() and dst.numel() * dst.element_size() >= fr_state_bytes(ctx)
+    return _check(_lib().fr_state_save(ctx, _ptr(dst)), "fr_state_save")
+
+
+def fr_state_load(ctx, src):
+    assert src.is_contiguous() and src.numel() * src.element_size() >= fr_state_bytes(ctx)
+    return _check(_lib().fr_state_load(ctx, _ptr(src)), "fr_state_load")
 
 
 def fr_reconstruct(ctx, out, w_clip=1.0, stream=None):

@@ -311,7 +311,10 @@ int fr::do_insert_ctx(fr_ctx *c, const void *images, fr_dtype dtype, const float
     const void *img = (const char *)images + (size_t)off * px_bytes;
     const float *r = rot + 9 * (size_t)off;
     Timing tm = c->tuner.begin(st);
-    int rc = run_config(c, s.config, img, f16, r, s.images, st);
+    // host-side fault injection (test hook): report a failed launch, enqueue nothing
+    int rc = (c->opt.fault_config > 0 && s.config == c->opt.fault_config - 1)
+                 ? FR_ERR_LAUNCH
+                 : run_config(c, s.config, img, f16, r, s.images, st);
     if (rc != FR_OK) {
       // the configuration could not launch: mark it and redo the work with the default
       cudaGetLastError();
@@ -513,6 +516,25 @@ int fr_finalize(fr_ctx *c, void *V, float *W, void *stream) {
   return FR_OK;
 }
 
+size_t fr_state_bytes(const fr_ctx *c) { return c ? 6 * c->plane * sizeof(float) : 0; }
+
+static int state_copy(fr_ctx *c, void *dst, const void *src) {
+  if (c->last_stream) FR_CUDA(cudaStreamSynchronize(c->last_stream));
+  FR_CUDA(cudaDeviceSynchronize());
+  FR_CUDA(cudaMemcpy(dst, src, fr_state_bytes(c), cudaMemcpyDefault));
+  return FR_OK;
+}
+
+int fr_state_save(fr_ctx *c, void *dst) {
+  if (!c || !dst) return FR_ERR_INVALID_ARG;
+  return state_copy(c, dst, c->acc);
+}
+
+int fr_state_load(fr_ctx *c, const void *src) {
+  if (!c || !src) return FR_ERR_INVALID_ARG;
+  return state_copy(c, c->acc, src);
+}
+
 int fr_retune(fr_ctx *c, int all) {
   if (!c) return FR_ERR_INVALID_ARG;
   c->tuner.harvest();
@@ -525,6 +547,7 @@ int fr_set_options(fr_ctx *c, const fr_options *o) {
   if (o->search < 0 || o->search > FR_SEARCH_MCMC || o->budget < 0 || o->steps_per_insert < 1)
     return FR_ERR_INVALID_ARG;
   if (o->forced_config >= (int)config_space().size()) return FR_ERR_INVALID_ARG;
+  if (o->fault_config < 0 || o->fault_config > (int)config_space().size()) return FR_ERR_INVALID_ARG;
   if (o->forced_config >= 0 && !config_valid(c, o->forced_config)) return FR_ERR_UNSUPPORTED;
   bool search_changed = o->search != c->opt.search || o->budget != c->opt.budget ||
                         o->seed != c->opt.seed;
