@@ -461,6 +461,13 @@ def run_ours(args):
             "kernel": L.fr_describe_config(best), "flops_per_update": FLOPS_PER_UPDATE,
             "peak_note": f"FP32 FMA peak: {sms} SMs x 128 lanes x 2 flops x {max_mhz:.0f} MHz (max SM clock)",
             "avg_launch_ms": 1e3 * per_launch_s, "updates_per_launch": ups_per_launch}
+    # measured check of the denominator: FMA-chain kernels that fill every SM
+    # (run after the timed region; fastest of 5 launches each)
+    tf1, _ = L.fr_probe_fp32_peak(False, 5)
+    tf2, _ = L.fr_probe_fp32_peak(True, 5)
+    roof["probe_tflops"] = {"fma_f32": tf1, "fma_f32x2": tf2,
+                            "note": "fr_probe_fp32_peak: 8 independent FMA chains per thread, "
+                                    "4 x 512 threads per SM, scalar and packed two-lane FMAs"}
 
     # ---- Algorithm 1's last step on the accumulated volume: symmetrise,
     # weight, inverse FFT (fr_reconstruct)
@@ -811,12 +818,18 @@ def launches_per_insert(L, cfg, n):
     return 2 * math.ceil(n / sub)  # scatter + merge per sub-batch
 
 
+GATHER_SOURCES = ("fr_device.cuh", "fr_gather.cuh", "fr_gather_common.cu", "fr_gather_launch.inc",
+                  "fr_gather_shapes.h", "fr_internal.h")
+
+
 def source_hash():
+    """Hash of the sources that define the gather kernels: a stored DRAM
+    traffic figure is reported only while they are unchanged."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1910_08498_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h", ".inc")):
+        if f in GATHER_SOURCES or (f.startswith("fr_gather_s") and f.endswith(".cu")):
             h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -129,6 +129,7 @@ def _lib():
             "fr_state_load": (i, [vp, vp]),
             "fr_prepare_images": (i, [vp, vp, i, i, vp, i, vp]),
             "fr_search_simulate": (i, [i, P(d), i, i, ctypes.c_uint64, i, P(i)]),
+            "fr_probe_fp32_peak": (i, [i, i, P(d), P(d), vp]),
             "fr_gemm_create": (i, [P(vp)]),
             "fr_gemm_destroy": (i, [vp]),
             "fr_gemm_set_tuning": (i, [vp, i, i, i, i, d, d, ctypes.c_uint64]),
@@ -219,6 +220,16 @@ def fr_insert_noalloc(S, images, rotations, V, W, a=1.9, alpha=15.0, n=None, str
     return _check(_lib().fr_insert_noalloc(int(S), float(a), float(alpha), _ptr(images),
                                            _dtype_of(images), _ptr(rotations), int(n), _ptr(V),
                                            _ptr(W), _stream(stream)), "fr_insert_noalloc")
+
+
+def fr_probe_fp32_peak(packed=False, repeats=5, stream=None) -> tuple[float, float]:
+    """Measured FP32 FMA peak: (TFLOP/s, ms) of the fastest of `repeats`
+    launches of the FMA-chain kernel (packed: two-lane f32x2 FMAs)."""
+    tf = ctypes.c_double()
+    ms = ctypes.c_double()
+    _check(_lib().fr_probe_fp32_peak(int(bool(packed)), int(repeats), ctypes.byref(tf),
+                                     ctypes.byref(ms), _stream(stream)), "fr_probe_fp32_peak")
+    return tf.value, ms.value
 
 
 def fr_search_simulate(search, ns_per_image, budget, seed=1, start=-1) -> list[int]:
