@@ -79,6 +79,9 @@ def parse():
     p.add_argument("--seed", type=int, default=5)
     p.add_argument("--profile-config", type=int, default=None,
                    help="profiling mode: time only this configuration id (no tuning, no baselines)")
+    p.add_argument("--gemm-profile", default=None, metavar="M,N,K,CONFIG",
+                   help="profiling mode: time one batched-GEMM configuration on one size "
+                        "(batch of about 512 MB of matrices)")
     p.add_argument("--phases", action="store_true",
                    help="profiling mode: also report the gather kernel's per-phase cycle counters")
     return p.parse_args()
@@ -875,10 +878,44 @@ def run_profile(args):
     return 0
 
 
+def run_gemm_profile(args):
+    """Small-case mode for ncu: warm-up then `steps` launches of one batched-GEMM
+    configuration on one size; prints its throughput (GB/s of A, B and C)."""
+    import torch
+
+    from paper_1910_08498_gb300 import _lib as L
+    m, n, k, cfg = (int(x) for x in args.gemm_profile.split(","))
+    if not L.fr_gemm_config_valid(cfg, m, n, k):
+        raise SystemExit(f"configuration {cfg} cannot run size {m}x{n}x{k}")
+    dev = torch.device("cuda", 0)
+    per = 4.0 * (m * k + k * n + m * n)
+    batch = int(min(1 << 26, max(1, 512e6 // per)))
+    g = torch.Generator(device=dev).manual_seed(args.seed)
+    A = torch.randn(batch, m, k, device=dev, generator=g)
+    B = torch.randn(batch, k, n, device=dev, generator=g)
+    C = torch.empty(batch, m, n, device=dev)
+    for _ in range(args.warmup):
+        L.fr_gemm_run_config(cfg, A, B, C)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(args.steps):
+        L.fr_gemm_run_config(cfg, A, B, C)
+    e.record()
+    torch.cuda.synchronize()
+    ms = s.elapsed_time(e) / args.steps
+    print(json.dumps({"config": L.fr_gemm_describe_config(cfg), "m": m, "n": n, "k": k, "batch": batch,
+                      "ms_per_launch": ms, "gbs": batch * per / (ms * 1e-3) / 1e9,
+                      "device_status": L.fr_gemm_device_status()}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.profile_config is not None:
         return run_profile(args)
+    if args.gemm_profile is not None:
+        return run_gemm_profile(args)
     if args.only_gemm:
         import torch
 

@@ -9,9 +9,20 @@
  *   instances stored one after the other (A: batch * m * k floats, ...).
  *   2 <= m, n, k <= 32.
  *
- * The kernel family is tuned over three dimensions (Sec. 4.2.5): Y, the rows
- * of C one thread computes (work-item coarsening), Z, the instances one CTA
- * computes, and whether C is staged in shared memory for coalesced stores.
+ * Two kernel families make up the configuration space (Sec. 4.2.5 tunes
+ * work-item coarsening, instances per work-group and local-memory staging):
+ *   - cooperative copies: Y, the rows of C one thread computes, Z, the
+ *     instances one CTA computes, and C staged in shared memory for
+ *     coalesced stores, or a persistent variant prefetching the next group
+ *     with cp.async (72 configurations);
+ *   - bulk copies: persistent CTAs stream groups of instances through a ring
+ *     of shared-memory stages filled by the bulk-copy engine (cp.async.bulk
+ *     with mbarrier completion), each thread computing a TY x TX register
+ *     tile of C, the group's C written back by one bulk store; tuned over TY,
+ *     TX in {1, 2, 4}, the rounds of the CTA's threads per group (1, 2, 4,
+ *     8) and the CTA size cap (128, 256) (72 configurations).
+ * Any 4-byte aligned A, B, C are accepted (the bulk copies move the 16-byte
+ * aligned interior of each block and plain loads and stores the ends).
  * The tuner is the insertion's non-blocking scheme (Sec. 3.2): a call with
  * tuning on splits its batch into sub-batches, each computed with the next
  * configuration of the search and timed with CUDA events, harvested without
@@ -52,6 +63,11 @@ int fr_gemm_run(fr_gemm_ctx *ctx, int m, int n, int k, const float *A, const flo
  * for this size). */
 int fr_gemm_run_config(int config, int m, int n, int k, const float *A, const float *B, float *C,
                        int batch, void *stream);
+/* Device-side status of the bulk-copy kernels: FR_ERR_TIMEOUT if, since the
+ * last call, a launch's bounded wait for a bulk copy gave up (after 1 s of
+ * the global timer; the results of that launch are invalid), else FR_OK.
+ * Waits for the device; clears the status.  FR_ERR_CUDA if it cannot be read. */
+int fr_gemm_device_status(void);
 /* Configuration space: count, description, validity for a size. */
 int fr_gemm_num_configs(void);
 int fr_gemm_describe_config(int id, char *buf, int len);

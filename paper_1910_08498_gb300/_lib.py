@@ -136,6 +136,7 @@ def _lib():
             "fr_gemm_run": (i, [vp, i, i, i, vp, vp, vp, i, vp]),
             "fr_gemm_run_config": (i, [i, i, i, i, vp, vp, vp, i, vp]),
             "fr_gemm_num_configs": (i, []),
+            "fr_gemm_device_status": (i, []),
             "fr_gemm_describe_config": (i, [i, ctypes.c_char_p, i]),
             "fr_gemm_config_valid": (i, [i, i, i, i]),
             "fr_gemm_report": (i, [vp, i, i, i, P(i), P(i), P(i), P(d), P(d)]),
@@ -499,6 +500,12 @@ def fr_gemm_run_config(config, A, B, C, stream=None):
     m, n, k, batch = _gemm_args(A, B, C)
     return _check(_lib().fr_gemm_run_config(int(config), m, n, k, _ptr(A), _ptr(B), _ptr(C), batch,
                                             _stream(stream)), "fr_gemm_run_config")
+
+
+def fr_gemm_device_status() -> int:
+    """FR_OK, or FR_ERR_TIMEOUT if a bulk-copy launch's bounded wait gave up
+    since the last call (clears it)."""
+    return _lib().fr_gemm_device_status()
 
 
 def fr_gemm_num_configs() -> int:

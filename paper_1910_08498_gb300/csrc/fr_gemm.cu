@@ -29,11 +29,28 @@
 #include "fr_internal.h"
 #include "fr_search.h"
 
+// set by a bulk-copy kernel whose bounded wait gave up (fr_gemm_device_status)
+static __device__ unsigned int g_gemm_error;
+
 namespace fr {
 namespace {
 
+struct BulkGeom {
+  int m, n, k, mk, kn, mn;
+  int Z;             // instances per group
+  int zt;            // instances computed at once (threads = zt * tiles)
+  int tiles, tcols;  // register tiles per instance, tiles per row of C
+  int ns;            // pipeline stages
+  int sa, sb, sc;    // floats per stage buffer of A, B and of the C buffer (incl. 4 of slack)
+  long long groups;
+  int batch;
+};
+
 struct GemmConfig {
   int y, z, stage, pipe;  // pipe: persistent CTAs, next group prefetched with cp.async
+  // bulk-copy family (bulk = 1): y x tx register tiles, r rounds of the CTA's
+  // threads per group, at most cap threads per CTA
+  int bulk = 0, tx = 1, r = 1, cap = 0;
 };
 
 const std::vector<GemmConfig> &gemm_space() {
@@ -44,12 +61,47 @@ const std::vector<GemmConfig> &gemm_space() {
         for (int st : {0, 1}) c.push_back(GemmConfig{y, z, st, 0});
         c.push_back(GemmConfig{y, z, 0, 1});
       }
+    for (int ty : {1, 2, 4})
+      for (int tx : {1, 2, 4})
+        for (int r : {1, 2, 4, 8})
+          for (int cap : {128, 256}) c.push_back(GemmConfig{ty, 0, 0, 0, 1, tx, r, cap});
     return c;
   }();
   return v;
 }
 
 int gemm_threads(const GemmConfig &c, int m, int n) { return n * ((m + c.y - 1) / c.y) * c.z; }
+
+// Launch geometry of a bulk-copy configuration for size (m, n, k); false if
+// it cannot run (too many tiles, fewer than 32 threads, too much shared memory).
+constexpr size_t BULK_SMEM_MAX = 226 * 1024;  // dynamic; static shared memory comes on top
+bool bulk_plan(const GemmConfig &c, int m, int n, int k, long long batch, BulkGeom *g,
+               size_t *smem, int *threads) {
+  BulkGeom q{};
+  q.m = m, q.n = n, q.k = k, q.mk = m * k, q.kn = k * n, q.mn = m * n;
+  q.tcols = (n + c.tx - 1) / c.tx;
+  q.tiles = ((m + c.y - 1) / c.y) * q.tcols;
+  if (q.tiles > c.cap) return false;
+  q.zt = c.cap / q.tiles;
+  const int t = q.zt * q.tiles;
+  if (t < 32) return false;
+  q.Z = q.zt * c.r;
+  auto round4 = [](long long f) { return (int)((f + 4 + 3) & ~3LL); };  // + shift slack
+  q.sa = round4((long long)q.Z * q.mk);
+  q.sb = round4((long long)q.Z * q.kn);
+  q.sc = round4((long long)q.Z * q.mn);
+  auto bytes = [&](int ns) { return 64 + 4 * ((size_t)ns * (q.sa + q.sb) + q.sc); };
+  // two stages: a deeper ring holds more shared memory per CTA and so fewer
+  // CTAs per SM, which measured slower (the compute phase needs the warps)
+  q.ns = 2;
+  if (bytes(q.ns) > BULK_SMEM_MAX) return false;
+  q.batch = (int)batch;
+  q.groups = (batch + q.Z - 1) / q.Z;
+  if (g) *g = q;
+  if (smem) *smem = bytes(q.ns);
+  if (threads) *threads = t;
+  return true;
+}
 
 size_t gemm_smem(const GemmConfig &c, int m, int n, int k) {
   if (c.pipe)  // two buffers of A and B, each with 16 B of alignment slack
@@ -61,6 +113,7 @@ bool gemm_valid(int id, int m, int n, int k) {
   if (id < 0 || id >= (int)gemm_space().size()) return false;
   if (m < 2 || m > 32 || n < 2 || n > 32 || k < 2 || k > 32) return false;
   const GemmConfig &c = gemm_space()[id];
+  if (c.bulk) return c.y <= m && c.tx <= n && bulk_plan(c, m, n, k, 1, nullptr, nullptr, nullptr);
   const int t = gemm_threads(c, m, n);
   if (c.y > m) return false;  // no thread would get a full strip
   return t >= 32 && t <= 1024 && gemm_smem(c, m, n, k) <= 48 * 1024;
@@ -220,6 +273,251 @@ __global__ void bgemm_pipe_kernel(int m, int n, int k, int z, const float *__res
   }
 }
 
+// ------------------------------------------------------------ bulk-copy family
+//
+// Persistent CTAs stream groups of Z consecutive instances through a ring of
+// two shared-memory stages.  One thread moves each group's A and B blocks (both
+// contiguous in memory) with the bulk-copy engine (cp.async.bulk, completion
+// counted in bytes on the stage's mbarrier), so the copy costs no per-element
+// instructions; the 16-byte-aligned interior of a block goes by bulk copy and
+// its at most 3 + 3 ragged floats by plain loads, each float landing at the
+// same address modulo 16 as in global memory.  Compute: a thread owns a
+// TY x TX register tile of C (rows clamped at the matrix edge), reading TY
+// values of A and TX values of B per step of the inner dimension.  The
+// group's C block is assembled in shared memory and written back by one bulk
+// store (ragged ends by plain stores).  Every mbarrier wait is bounded by
+// GEMM_WAIT_NS of the global timer; a wait that gives up records
+// FR_ERR_TIMEOUT in g_gemm_error (fr_gemm_device_status) and the CTA stops.
+
+constexpr long long GEMM_WAIT_NS = 1000000000LL;  // 1 s
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// true once the phase with the given parity has completed; false after
+// GEMM_WAIT_NS (try_wait itself returns after a bounded, hardware-defined time)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((long long)(global_ns() - t0) > GEMM_WAIT_NS) return false;
+  }
+}
+
+__device__ __forceinline__ void bulk_load(float *dst, const float *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_store(float *dst, const float *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_addr(src)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// generic-proxy shared-memory writes made visible to the bulk-copy engine
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// A contiguous block of `count` floats at global address src, as the bulk
+// copy sees it: `shift` = (src / 4) mod 4 (element e sits at buf[shift + e]),
+// the 16-byte aligned interior [lo, hi) of element indices and its bytes.
+struct BlockSpan {
+  int shift, lo, hi;
+  __device__ BlockSpan(const float *src, int count) {
+    shift = (int)((reinterpret_cast<uintptr_t>(src) >> 2) & 3);
+    lo = min(count, (4 - shift) & 3);
+    hi = max(lo, ((shift + count) & ~3) - shift);
+  }
+  __device__ uint32_t bytes() const { return 4u * (uint32_t)(hi - lo); }
+};
+
+
+template <int TY, int TX>
+__global__ void __launch_bounds__(256) bgemm_bulk_kernel(const BulkGeom g, const float *__restrict__ A,
+                                                          const float *__restrict__ B,
+                                                          float *__restrict__ C) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smraw);          // g.ns barriers
+  float *sbase = reinterpret_cast<float *>(smraw + 64);          // 16-byte aligned
+  float *sC = sbase + (size_t)g.ns * (g.sa + g.sb);
+  __shared__ int s_abort;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < g.ns; ++s) mbar_init(&bar[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    fence_proxy_async();
+    s_abort = 0;
+  }
+  __syncthreads();
+
+  auto stageA = [&](int s) { return sbase + (size_t)s * (g.sa + g.sb); };
+  auto stageB = [&](int s) { return sbase + (size_t)s * (g.sa + g.sb) + g.sa; };
+  // thread 0: start the bulk copies of group gi into stage s
+  auto issue = [&](long long gi, int s) {
+    const long long b0 = gi * g.Z;
+    const int nb = (int)min((long long)g.Z, (long long)g.batch - b0);
+    const float *a = A + b0 * g.mk, *b = B + b0 * g.kn;
+    const BlockSpan sa(a, nb * g.mk), sb(b, nb * g.kn);
+    mbar_arrive_expect_tx(&bar[s], sa.bytes() + sb.bytes());
+    if (sa.hi > sa.lo) bulk_load(stageA(s) + sa.shift + sa.lo, a + sa.lo, sa.bytes(), &bar[s]);
+    if (sb.hi > sb.lo) bulk_load(stageB(s) + sb.shift + sb.lo, b + sb.lo, sb.bytes(), &bar[s]);
+  };
+  // all threads: the ragged ends of group gi's blocks by plain loads
+  auto edges_in = [&](long long gi, int s) {
+    if (tid >= 32) return;
+    const long long b0 = gi * g.Z;
+    const int nb = (int)min((long long)g.Z, (long long)g.batch - b0);
+    const bool isA = tid < 16;
+    const float *src = isA ? A + b0 * g.mk : B + b0 * g.kn;
+    const int cnt = nb * (isA ? g.mk : g.kn);
+    float *dst = isA ? stageA(s) : stageB(s);
+    const BlockSpan sp(src, cnt);
+    const int q = tid & 15;  // q < 4: head element, 4 <= q < 8: tail element
+    int e = -1;
+    if (sp.hi > sp.lo) {
+      if (q < 4 && q < sp.lo) e = q;
+      else if (q >= 4 && q < 8 && sp.hi + (q - 4) < cnt) e = sp.hi + (q - 4);
+    } else if (q < cnt) {  // no interior (fewer than 8 floats): all by plain loads
+      e = q;
+    }
+    if (e >= 0) dst[sp.shift + e] = __ldg(src + e);
+  };
+
+  const long long G = g.groups;
+  if (tid == 0)
+    for (int s = 0; s < g.ns; ++s) {
+      const long long gi = blockIdx.x + (long long)s * gridDim.x;
+      if (gi < G) issue(gi, s);
+    }
+  const int tile = tid % g.tiles, tz = tid / g.tiles;
+  const int tr = tile / g.tcols, tc = tile - tr * g.tcols;
+  const int r0 = tr * TY, c0 = tc * TX;
+  const bool active = tz < g.zt;
+  int i = 0;
+  for (long long gi = blockIdx.x; gi < G; gi += gridDim.x, ++i) {
+    const int s = i % g.ns;
+    const uint32_t parity = (uint32_t)((i / g.ns) & 1);
+    edges_in(gi, s);
+    if (tid == 0) {
+      bulk_wait_read_all();  // the previous group's C store has read sC
+      if (!mbar_wait_bounded(&bar[s], parity)) s_abort = 1;
+    }
+    __syncthreads();
+    if (s_abort) break;
+    const long long b0 = gi * g.Z;
+    const int nb = (int)min((long long)g.Z, (long long)g.batch - b0);
+    const float *gA = A + b0 * g.mk, *gB = B + b0 * g.kn;
+    float *gC = C + b0 * g.mn;
+    const BlockSpan spA(gA, nb * g.mk), spB(gB, nb * g.kn), spC(gC, nb * g.mn);
+    const float *sA = stageA(s) + spA.shift, *sB = stageB(s) + spB.shift;
+    float *sCc = sC + spC.shift;
+    if (active) {
+      int arow[TY], bcol[TX];
+#pragma unroll
+      for (int r = 0; r < TY; ++r) arow[r] = min(r0 + r, g.m - 1) * g.k;
+#pragma unroll
+      for (int c = 0; c < TX; ++c) bcol[c] = min(c0 + c, g.n - 1);
+      for (int t = tz; t < nb; t += g.zt) {
+        const float *a = sA + t * g.mk, *b = sB + t * g.kn;
+        float acc[TY][TX];
+#pragma unroll
+        for (int r = 0; r < TY; ++r)
+#pragma unroll
+          for (int c = 0; c < TX; ++c) acc[r][c] = 0.f;
+#pragma unroll 2
+        for (int p = 0; p < g.k; ++p) {
+          float av[TY], bv[TX];
+#pragma unroll
+          for (int r = 0; r < TY; ++r) av[r] = a[arow[r] + p];
+#pragma unroll
+          for (int c = 0; c < TX; ++c) bv[c] = b[p * g.n + bcol[c]];
+#pragma unroll
+          for (int r = 0; r < TY; ++r)
+#pragma unroll
+            for (int c = 0; c < TX; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+        }
+        float *cc = sCc + t * g.mn;
+#pragma unroll
+        for (int r = 0; r < TY; ++r)
+          if (r0 + r < g.m)
+#pragma unroll
+            for (int c = 0; c < TX; ++c)
+              if (c0 + c < g.n) cc[(r0 + r) * g.n + c0 + c] = acc[r][c];
+      }
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      if (spC.hi > spC.lo) {
+        bulk_store(gC + spC.lo, sCc + spC.lo, spC.bytes());
+        bulk_commit();
+      }
+      const long long gn = gi + (long long)g.ns * gridDim.x;
+      if (gn < G) issue(gn, s);
+    }
+    // ragged ends of C by plain stores (sC is not rewritten before the next barrier)
+    if (tid < 8) {
+      const int q = tid;
+      const int cnt = nb * g.mn;
+      int e = -1;
+      if (spC.hi > spC.lo) {
+        if (q < 4 && q < spC.lo) e = q;
+        else if (q >= 4 && spC.hi + (q - 4) < cnt) e = spC.hi + (q - 4);
+      } else if (q < cnt) {
+        e = q;
+      }
+      if (e >= 0) gC[e] = sCc[e];
+    }
+  }
+  if (tid == 0) {
+    if (s_abort) {
+      atomicOr(&g_gemm_error, 1u);
+      // bounded waits for the copies still in flight (groups i .. i + ns - 1),
+      // so that none lands after the CTA's shared memory is released
+      for (int j = 0; j < g.ns; ++j) {
+        const long long gj = blockIdx.x + (long long)(i + j) * gridDim.x;
+        if (gj < G) mbar_wait_bounded(&bar[(i + j) % g.ns], (uint32_t)(((i + j) / g.ns) & 1));
+      }
+    }
+    bulk_wait_all();
+  }
+}
+
 template <int Y, int STAGE>
 cudaError_t launch_t(const GemmConfig &c, int m, int n, int k, const float *A, const float *B,
                      float *C, int batch, cudaStream_t st) {
@@ -248,10 +546,52 @@ cudaError_t launch_pipe(const GemmConfig &c, int m, int n, int k, const float *A
   return cudaGetLastError();
 }
 
+template <int TY, int TX>
+cudaError_t launch_bulk(const GemmConfig &c, int m, int n, int k, const float *A, const float *B,
+                        float *C, int batch, cudaStream_t st) {
+  BulkGeom g;
+  size_t smem = 0;
+  int threads = 0;
+  if (!bulk_plan(c, m, n, k, batch, &g, &smem, &threads)) return cudaErrorInvalidValue;
+  auto fn = bgemm_bulk_kernel<TY, TX>;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [&] {
+    attr = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BULK_SMEM_MAX);
+    if (attr == cudaSuccess)
+      attr = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  cudaSharedmemCarveoutMaxShared);
+  });
+  if (attr != cudaSuccess) return attr;
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const long long grid = std::min<long long>(g.groups, (long long)per_sm * sms);
+  fn<<<(unsigned)grid, threads, smem, st>>>(g, A, B, C);
+  return cudaGetLastError();
+}
+
 cudaError_t gemm_launch(int id, int m, int n, int k, const float *A, const float *B, float *C,
                         int batch, cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
   const GemmConfig &c = gemm_space()[id];
+  if (c.bulk) {
+    switch (c.y * 8 + c.tx) {
+      case 9: return launch_bulk<1, 1>(c, m, n, k, A, B, C, batch, st);
+      case 10: return launch_bulk<1, 2>(c, m, n, k, A, B, C, batch, st);
+      case 12: return launch_bulk<1, 4>(c, m, n, k, A, B, C, batch, st);
+      case 17: return launch_bulk<2, 1>(c, m, n, k, A, B, C, batch, st);
+      case 18: return launch_bulk<2, 2>(c, m, n, k, A, B, C, batch, st);
+      case 20: return launch_bulk<2, 4>(c, m, n, k, A, B, C, batch, st);
+      case 33: return launch_bulk<4, 1>(c, m, n, k, A, B, C, batch, st);
+      case 34: return launch_bulk<4, 2>(c, m, n, k, A, B, C, batch, st);
+      case 36: return launch_bulk<4, 4>(c, m, n, k, A, B, C, batch, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   if (c.pipe) {
     switch (c.y) {
       case 1: return launch_pipe<1>(c, m, n, k, A, B, C, batch, st);
@@ -272,6 +612,16 @@ cudaError_t gemm_launch(int id, int m, int n, int k, const float *A, const float
     case 17: return launch_t<8, 1>(c, m, n, k, A, B, C, batch, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// Neighbours for the annealing and Metropolis walks: configurations of one
+// family that differ in exactly one tuning dimension; across the two families
+// (the family being one more dimension), those with the same row coarsening.
+bool gemm_neighbours(const GemmConfig &x, const GemmConfig &y) {
+  if (x.bulk != y.bulk) return x.y == y.y;
+  if (x.bulk)
+    return (x.y != y.y) + (x.tx != y.tx) + (x.r != y.r) + (x.cap != y.cap) == 1;
+  return (x.y != y.y) + (x.z != y.z) + (x.stage != y.stage) + (x.pipe != y.pipe) == 1;
 }
 
 double instance_bytes(int m, int n, int k) { return 4.0 * ((double)m * k + (double)k * n + (double)m * n); }
@@ -394,8 +744,7 @@ struct fr_gemm_ctx {
       for (int a : valid)
         for (int b : valid) {
           const GemmConfig &x = gemm_space()[a], &y = gemm_space()[b];
-          if ((x.y != y.y) + (x.z != y.z) + (x.stage != y.stage) + (x.pipe != y.pipe) == 1)
-            ks.walker.nbr[a].push_back(b);
+          if (gemm_neighbours(x, y)) ks.walker.nbr[a].push_back(b);
         }
       ks.walker.anneal = search == FR_SEARCH_ANNEALING;
       ks.walker.T = ks.walker.anneal ? 0.2 : 0.1;
@@ -452,13 +801,27 @@ int fr_gemm_set_tuning(fr_gemm_ctx *c, int tuning, int search, int budget, int s
   return FR_OK;
 }
 
+int fr_gemm_device_status(void) {
+  unsigned int v = 0, zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_gemm_error, sizeof(v));
+  if (e == cudaSuccess && v) e = cudaMemcpyToSymbol(g_gemm_error, &zero, sizeof(zero));
+  if (e != cudaSuccess) {
+    fr_note_cuda_error((int)e);
+    return FR_ERR_CUDA;
+  }
+  return v ? FR_ERR_TIMEOUT : FR_OK;
+}
+
 int fr_gemm_num_configs(void) { return (int)gemm_space().size(); }
 
 int fr_gemm_describe_config(int id, char *buf, int len) {
   if (id < 0 || id >= (int)gemm_space().size() || !buf || len < 1) return FR_ERR_INVALID_ARG;
   const GemmConfig &c = gemm_space()[id];
-  std::snprintf(buf, len, "bgemm y=%d z=%d %s", c.y, c.z,
-                c.pipe ? "pipelined" : (c.stage ? "stage=1" : "stage=0"));
+  if (c.bulk)
+    std::snprintf(buf, len, "bgemm bulk ty=%d tx=%d r=%d t=%d", c.y, c.tx, c.r, c.cap);
+  else
+    std::snprintf(buf, len, "bgemm y=%d z=%d %s", c.y, c.z,
+                  c.pipe ? "pipelined" : (c.stage ? "stage=1" : "stage=0"));
   return FR_OK;
 }
 

@@ -81,3 +81,43 @@ def test_stop_rule_bandwidth_target(search):
         _check(C, A, B)
     finally:
         L.fr_gemm_destroy(ctx)
+
+
+def _bulk_configs(m, n, k):
+    return [c for c in range(L.fr_gemm_num_configs())
+            if "bulk" in L.fr_gemm_describe_config(c) and L.fr_gemm_config_valid(c, m, n, k)]
+
+
+@pytest.mark.parametrize("m,n,k", [(2, 2, 2), (3, 5, 7), (9, 12, 32), (31, 30, 29)])
+@pytest.mark.parametrize("off", [1, 2, 3])
+def test_bulk_copies_at_unaligned_offsets(m, n, k, off):
+    """Blocks that start at any 4-byte offset: the bulk-copy kernels move the
+    16-byte aligned interior and the ragged ends separately; nothing outside
+    the caller's C range is written."""
+    batch = 389
+    A, B = _data(m, n, k, batch + off, 7 * m + n + k + off)
+    Ad, Bd = A.cuda(), B.cuda()
+    cfgs = _bulk_configs(m, n, k)
+    assert cfgs
+    for cfg in cfgs:
+        Cfull = torch.full((batch + off + 1, m, n), float("nan"), device="cuda")
+        L.fr_gemm_run_config(cfg, Ad[off:], Bd[off:], Cfull[off:off + batch])
+        torch.cuda.synchronize()
+        _check(Cfull[off:off + batch], A[off:], B[off:])
+        assert torch.isnan(Cfull[:off]).all() and torch.isnan(Cfull[off + batch:]).all(), \
+            L.fr_gemm_describe_config(cfg)
+    assert L.fr_gemm_device_status() == L.FR_OK
+
+
+@pytest.mark.parametrize("batch", [1, 2, 3, 5, 4099])
+def test_bulk_copies_ragged_batches(batch):
+    """Batches from one instance up to many groups per CTA (the last group partial)."""
+    m, n, k = 7, 3, 5
+    A, B = _data(m, n, k, batch, batch)
+    Ad, Bd = A.cuda(), B.cuda()
+    for cfg in _bulk_configs(m, n, k):
+        C = torch.full((batch, m, n), float("nan"), device="cuda")
+        L.fr_gemm_run_config(cfg, Ad, Bd, C)
+        torch.cuda.synchronize()
+        _check(C, A, B)
+    assert L.fr_gemm_device_status() == L.FR_OK
