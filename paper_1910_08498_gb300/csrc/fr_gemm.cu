@@ -450,8 +450,11 @@ __global__ void __launch_bounds__(256) bgemm_bulk_kernel(const BulkGeom g, const
       int arow[TY], bcol[TX];
 #pragma unroll
       for (int r = 0; r < TY; ++r) arow[r] = min(r0 + r, g.m - 1) * g.k;
+      // columns past n are not clamped: they read at most TX - 1 floats past a
+      // row of B, which stays inside this CTA's shared memory (the buffer's
+      // slack, or the next region), and their results are never stored
 #pragma unroll
-      for (int c = 0; c < TX; ++c) bcol[c] = min(c0 + c, g.n - 1);
+      for (int c = 0; c < TX; ++c) bcol[c] = c0 + c;
       for (int t = tz; t < nb; t += g.zt) {
         const float *a = sA + t * g.mk, *b = sB + t * g.kn;
         float acc[TY][TX];
