@@ -9,7 +9,9 @@
 // the CTA's C block is assembled in shared memory and written back with
 // coalesced stores; otherwise each thread stores its Y values directly.  The
 // pipelined variant keeps a grid of resident CTAs that prefetch their next
-// group of instances with cp.async while computing the current one.
+// group of instances with cp.async while computing the current one.  The
+// bulk-copy family (bgemm_bulk_kernel, below) moves the blocks with the
+// bulk-copy engine instead and computes register tiles of C.
 #include <cuda_runtime.h>
 
 #include <algorithm>
