@@ -121,3 +121,37 @@ def test_bulk_copies_ragged_batches(batch):
         torch.cuda.synchronize()
         _check(C, A, B)
     assert L.fr_gemm_device_status() == L.FR_OK
+
+
+@pytest.mark.parametrize("m,n,k", [(23, 22, 21), (6, 14, 2)])
+def test_full_size_batch_sampled_instances(m, n, k):
+    """The batch size the study times (about 512 MB of matrices): every bulk
+    configuration, and the tuner, checked on sampled instances."""
+    per = 4 * (m * k + k * n + m * n)
+    batch = int(512e6 // per)
+    g = torch.Generator(device="cuda").manual_seed(m * n * k)
+    Ad = torch.randn(batch, m, k, device="cuda", generator=g)
+    Bd = torch.randn(batch, k, n, device="cuda", generator=g)
+    idx = torch.arange(0, batch, 997)
+    idx = torch.cat([idx, torch.tensor([batch - 1])])
+    As, Bs = Ad[idx].cpu(), Bd[idx].cpu()
+    C = torch.empty(batch, m, n, device="cuda")
+    for cfg in _bulk_configs(m, n, k):
+        C.fill_(float("nan"))
+        L.fr_gemm_run_config(cfg, Ad, Bd, C)
+        torch.cuda.synchronize()
+        _check(C[idx], As, Bs)
+        assert not torch.isnan(C).any(), L.fr_gemm_describe_config(cfg)
+    ctx = L.fr_gemm_create()
+    try:
+        L.fr_gemm_set_tuning(ctx, tuning=1, search=L.FR_SEARCH_RANDOM, budget=20, steps=2)
+        for _ in range(12):
+            C.fill_(float("nan"))
+            L.fr_gemm_run(ctx, Ad, Bd, C)
+        torch.cuda.synchronize()
+        _check(C[idx], As, Bs)
+        assert not torch.isnan(C).any()
+        assert L.fr_gemm_report(ctx, m, n, k)["tuned"] == 1
+    finally:
+        L.fr_gemm_destroy(ctx)
+    assert L.fr_gemm_device_status() == L.FR_OK
