@@ -203,9 +203,10 @@ int fr_finalize(fr_ctx *ctx, void *V, float *W, void *stream);
  *          pixel (S/2, S/2) instead of (0, 0)); FR_F16 rounds to nearest half.
  *   n      0 <= n <= 2^24 (0: nothing).
  * The transforms are the CUDA toolkit's cuFFT (batched R2C, loaded at run
- * time; FR_ERR_UNSUPPORTED if it cannot be loaded), in chunks of 256 images;
- * the sign and the FP16 conversion are a kernel of this library.  Allocates on
- * first use the plans and, for FR_F16, a staging buffer of 256 transforms.
+ * time; FR_ERR_UNSUPPORTED if it cannot be loaded), in chunks of about 256 MB
+ * of spectra (at least 256 images); the sign and the FP16 conversion are a
+ * kernel of this library.  Allocates on first use the plans and, for FR_F16,
+ * a staging buffer of one chunk.
  * Work is enqueued on `stream`. */
 int fr_prepare_images(fr_ctx *ctx, const float *real, int n, int center, void *out,
                       fr_dtype dtype, void *stream);

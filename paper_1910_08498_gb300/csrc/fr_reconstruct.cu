@@ -114,22 +114,36 @@ namespace {
 // The R2C output of a chunk of images, [m][S][S/2+1] float2 in rfft2 order,
 // into the insertion input: multiplied by (-1)^(kx + j) when centring (the
 // image origin moved from pixel (0, 0) to (S/2, S/2)), stored as float2 or
-// half2.
+// half2.  Two entries per thread (16-byte loads; `total` is even since S is).
+// Entry o = (image * S + j) * NX + kx; when NX = S/2 + 1 is odd (S a multiple
+// of 4) the parity of kx + j is that of o, so the sign needs no division.
 template <int F16>
 __global__ void stage_kernel(const float2 *__restrict__ spec, size_t total, int NX, int center,
                              void *__restrict__ out) {
-  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < total;
-       o += (size_t)gridDim.x * blockDim.x) {
-    float2 v = spec[o];
+  const size_t pairs = total / 2;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < pairs;
+       i += (size_t)gridDim.x * blockDim.x) {
+    float4 v = reinterpret_cast<const float4 *>(spec)[i];
     if (center) {
-      const int kx = (int)(o % NX);
-      const int j = (int)((o / NX) % (size_t)(2 * (NX - 1)));
-      if ((kx + j) & 1) v = make_float2(-v.x, -v.y);
+      bool neg0 = false, neg1 = true;  // entry 2i is even, 2i + 1 odd
+      if (!(NX & 1)) {
+        const size_t o = 2 * i, row = o / (size_t)NX;
+        const int kx = (int)(o - row * NX);
+        neg0 = ((kx + (int)(row & 1)) & 1) != 0;
+        neg1 = kx + 1 < NX ? !neg0 : ((row + 1) & 1) != 0;  // entry 2i + 1 opens row + 1
+      }
+      if (neg0) v.x = -v.x, v.y = -v.y;
+      if (neg1) v.z = -v.z, v.w = -v.w;
     }
-    if (F16)
-      reinterpret_cast<__half2 *>(out)[o] = __floats2half2_rn(v.x, v.y);
-    else
-      reinterpret_cast<float2 *>(out)[o] = v;
+    if (F16) {
+      const __half2 h0 = __floats2half2_rn(v.x, v.y), h1 = __floats2half2_rn(v.z, v.w);
+      uint2 u;
+      u.x = *reinterpret_cast<const unsigned int *>(&h0);
+      u.y = *reinterpret_cast<const unsigned int *>(&h1);
+      reinterpret_cast<uint2 *>(out)[i] = u;
+    } else {
+      reinterpret_cast<float4 *>(out)[i] = v;
+    }
   }
 }
 
@@ -213,7 +227,10 @@ extern "C" int fr_prepare_images(fr_ctx *c, const float *real, int n, int center
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int S = c->S, NX = S / 2 + 1;
   const size_t px_real = (size_t)S * S, px_spec = (size_t)S * NX;
-  constexpr int CHUNK = 256;
+  // images per transform: about 256 MB of spectra per cuFFT launch (fewer,
+  // larger launches measured faster than chunks of 256 images at S = 256),
+  // and at least 256 images
+  const int CHUNK = (int)std::max<size_t>(256, ((size_t)256 << 20) / (px_spec * sizeof(float2)));
   const bool direct = dtype == FR_F32;  // FP32: transform straight into out
   if (!direct && !c->prep_ws) {
     cudaError_t e = cudaMalloc(&c->prep_ws, (size_t)CHUNK * px_spec * sizeof(float2));
@@ -239,7 +256,7 @@ extern "C" int fr_prepare_images(fr_ctx *c, const float *real, int n, int center
     if (!direct || center) {
       const size_t total = (size_t)m * px_spec;
       const int threads = 256;
-      const int blocks = (int)std::min<size_t>((total + threads - 1) / threads, (size_t)std::max(sms, 1) * 8);
+      const int blocks = (int)std::min<size_t>((total / 2 + threads - 1) / threads, (size_t)std::max(sms, 1) * 8);
       if (direct)
         stage_kernel<0><<<blocks, threads, 0, st>>>(dst, total, NX, center, dst);
       else

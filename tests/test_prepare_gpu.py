@@ -23,7 +23,8 @@ def _real(S, n, seed):
     return torch.randn(n, S, S, generator=g, dtype=torch.float32)
 
 
-@pytest.mark.parametrize("S,n,center", [(32, 300, False), (32, 300, True), (48, 257, True), (64, 5, False)])
+@pytest.mark.parametrize("S,n,center", [(32, 300, False), (32, 300, True), (48, 257, True), (64, 5, False),
+                                         (30, 301, True), (14, 9, True)])
 def test_prepare_fp32(S, n, center):
     real = _real(S, n, S + n)
     ctx = L.fr_create(S)
@@ -38,9 +39,9 @@ def test_prepare_fp32(S, n, center):
     assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
 
 
-def test_prepare_fp16():
-    S, n = 32, 70
-    real = _real(S, n, 5)
+@pytest.mark.parametrize("S,n", [(32, 70), (30, 33)])
+def test_prepare_fp16(S, n):
+    real = _real(S, n, 5 + S)
     ctx = L.fr_create(S)
     try:
         out = torch.empty(n, S, S // 2 + 1, 2, dtype=torch.float16, device="cuda")
@@ -53,6 +54,35 @@ def test_prepare_fp16():
     ref2 = np.stack([ref.real, ref.imag], -1)
     bound = np.abs(ref2) * 2.0 ** -11 + 1e-5 * np.max(np.abs(ref))
     assert np.all(np.abs(got - ref2) <= bound)
+
+
+@pytest.mark.parametrize("f16", [False, True])
+def test_prepare_across_a_chunk_boundary(f16):
+    """S = 256: the transforms run in chunks of about 256 MB of spectra (1016
+    images here); images on both sides of the first boundary and the last
+    image of the tail chunk match the reference."""
+    S, n = 256, 1100
+    real = _real(S, n, 77)
+    ctx = L.fr_create(S)
+    try:
+        if f16:
+            out = torch.empty(n, S, S // 2 + 1, 2, dtype=torch.float16, device="cuda")
+        else:
+            out = torch.empty(n, S, S // 2 + 1, dtype=torch.complex64, device="cuda")
+        L.fr_prepare_images(ctx, real.cuda(), out, center=True)
+        torch.cuda.synchronize()
+    finally:
+        L.fr_destroy(ctx)
+    pick = [0, 1015, 1016, 1099]
+    ref = recon.image_spectra(real[pick].numpy(), center=True)
+    got = out[pick].cpu()
+    if f16:
+        got = got.float().numpy().astype(np.float64)
+        ref2 = np.stack([ref.real, ref.imag], -1)
+        assert np.all(np.abs(got - ref2) <= np.abs(ref2) * 2.0 ** -11 + 1e-5 * np.max(np.abs(ref)))
+    else:
+        got = got.numpy().astype(np.complex128)
+        assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
 
 
 def test_prepared_images_insert_like_the_oracle():
