@@ -101,11 +101,16 @@ typedef struct fr_options {
     int forced_config;   /* >= 0: always use this configuration id; -1 (default): tuner decides */
     uint64_t seed;       /* seed of the search order (default 1) */
     int debug;           /* bit 0: synchronise after every launch and check the device error
-                            word; bit 1: collect gather phase counters */
+                            word; bit 1: collect gather phase counters; bit 2: an NVTX range
+                            around every insertion step (named by configuration and images) */
     int fault_config;    /* test hook (host-side fault injection): > 0 makes every launch of
                             configuration fault_config - 1 report a launch failure without
                             enqueuing work, so the fallback path runs; 0 (default): none */
-    int reserved[7];
+    int fault_alloc;     /* test hook (host-side fault injection): k > 0 makes the k-th device
+                            allocation the insertion path attempts after this call (work-unit
+                            lists, scratch) fail as out of memory; the step then falls back as
+                            for a failed launch.  0 (default): none */
+    int reserved[6];
 } fr_options;
 
 /* What the tuner has done for the context's current key. */

@@ -44,7 +44,7 @@ class fr_options(ctypes.Structure):
     _fields_ = [("tuning", ctypes.c_int), ("search", ctypes.c_int), ("budget", ctypes.c_int),
                 ("steps_per_insert", ctypes.c_int), ("forced_config", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("debug", ctypes.c_int), ("fault_config", ctypes.c_int),
-                ("reserved", ctypes.c_int * 7)]
+                ("fault_alloc", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
 
 
 class fr_report(ctypes.Structure):
@@ -137,6 +137,7 @@ def _lib():
             "fr_gemm_run_config": (i, [i, i, i, i, vp, vp, vp, i, vp]),
             "fr_gemm_num_configs": (i, []),
             "fr_gemm_device_status": (i, []),
+            "fr_gemm_set_wait_limit": (i, [ctypes.c_longlong]),
             "fr_gemm_describe_config": (i, [i, ctypes.c_char_p, i]),
             "fr_gemm_config_valid": (i, [i, i, i, i]),
             "fr_gemm_report": (i, [vp, i, i, i, P(i), P(i), P(i), P(d), P(d)]),
@@ -506,6 +507,11 @@ def fr_gemm_device_status() -> int:
     """FR_OK, or FR_ERR_TIMEOUT if a bulk-copy launch's bounded wait gave up
     since the last call (clears it)."""
     return _lib().fr_gemm_device_status()
+
+
+def fr_gemm_set_wait_limit(ns: int):
+    """Test hook: limit (ns) of the bulk-copy kernels' waits for their copies."""
+    return _check(_lib().fr_gemm_set_wait_limit(int(ns)), "fr_gemm_set_wait_limit")
 
 
 def fr_gemm_num_configs() -> int:

@@ -29,6 +29,7 @@ struct fr_ctx {
   cudaStream_t last_stream = nullptr;
   unsigned long long images = 0;
   int launches = 0;
+  int alloc_countdown = 0;  // fault injection: allocations left before the injected failure
   fr::Tuner tuner;
   // gather work-unit lists, keyed by (brick shape, n); most recent first
   struct Units {

@@ -33,6 +33,9 @@
 
 // set by a bulk-copy kernel whose bounded wait gave up (fr_gemm_device_status)
 static __device__ unsigned int g_gemm_error;
+// limit of a bulk-copy kernel's waits for its copies, in ns of the global timer
+// (fr_gemm_set_wait_limit; 1 s by default)
+static __device__ long long g_gemm_wait_ns = 1000000000LL;
 
 namespace fr {
 namespace {
@@ -288,8 +291,10 @@ __global__ void bgemm_pipe_kernel(int m, int n, int k, int z, const float *__res
 // values of A and TX values of B per step of the inner dimension.  The
 // group's C block is assembled in shared memory and written back by one bulk
 // store (ragged ends by plain stores).  Every mbarrier wait is bounded by
-// GEMM_WAIT_NS of the global timer; a wait that gives up records
-// FR_ERR_TIMEOUT in g_gemm_error (fr_gemm_device_status) and the CTA stops.
+// g_gemm_wait_ns of the global timer (GEMM_WAIT_NS unless a test sets it with
+// fr_gemm_set_wait_limit); a wait that gives up records
+// FR_ERR_TIMEOUT in g_gemm_error (fr_gemm_device_status) and the CTA stops
+// after waiting (bounded by GEMM_WAIT_NS) for its copies still in flight.
 
 constexpr long long GEMM_WAIT_NS = 1000000000LL;  // 1 s
 
@@ -313,11 +318,28 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                : "memory");
 }
 
-// true once the phase with the given parity has completed; false after
-// GEMM_WAIT_NS (try_wait itself returns after a bounded, hardware-defined time)
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// true once the phase with the given parity has completed; false once a poll
+// finds it incomplete limit_ns or more after the start (limit 0: at the first
+// such poll).  Between polls try_wait suspends the thread for a bounded,
+// hardware-defined time.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  long long limit_ns) {
   const unsigned long long t0 = global_ns();
   while (true) {
+    if (mbar_test_wait(bar, parity)) return true;
+    if ((long long)(global_ns() - t0) >= limit_ns) return false;
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -327,7 +349,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
         : "r"(smem_addr(bar)), "r"(parity)
         : "memory");
     if (ok) return true;
-    if ((long long)(global_ns() - t0) > GEMM_WAIT_NS) return false;
   }
 }
 
@@ -379,6 +400,7 @@ __global__ void __launch_bounds__(256) bgemm_bulk_kernel(const BulkGeom g, const
   float *sC = sbase + (size_t)g.ns * (g.sa + g.sb);
   __shared__ int s_abort;
   const int tid = threadIdx.x;
+  const long long wait_ns = tid == 0 ? g_gemm_wait_ns : 0;
   if (tid == 0) {
     for (int s = 0; s < g.ns; ++s) mbar_init(&bar[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -437,7 +459,7 @@ __global__ void __launch_bounds__(256) bgemm_bulk_kernel(const BulkGeom g, const
     edges_in(gi, s);
     if (tid == 0) {
       bulk_wait_read_all();  // the previous group's C store has read sC
-      if (!mbar_wait_bounded(&bar[s], parity)) s_abort = 1;
+      if (!mbar_wait_bounded(&bar[s], parity, wait_ns)) s_abort = 1;
     }
     __syncthreads();
     if (s_abort) break;
@@ -516,7 +538,8 @@ __global__ void __launch_bounds__(256) bgemm_bulk_kernel(const BulkGeom g, const
       // so that none lands after the CTA's shared memory is released
       for (int j = 0; j < g.ns; ++j) {
         const long long gj = blockIdx.x + (long long)(i + j) * gridDim.x;
-        if (gj < G) mbar_wait_bounded(&bar[(i + j) % g.ns], (uint32_t)(((i + j) / g.ns) & 1));
+        if (gj < G)
+          mbar_wait_bounded(&bar[(i + j) % g.ns], (uint32_t)(((i + j) / g.ns) & 1), GEMM_WAIT_NS);
       }
     }
     bulk_wait_all();
@@ -815,6 +838,16 @@ int fr_gemm_device_status(void) {
     return FR_ERR_CUDA;
   }
   return v ? FR_ERR_TIMEOUT : FR_OK;
+}
+
+int fr_gemm_set_wait_limit(long long ns) {
+  if (ns < 0 || ns > 10000000000LL) return FR_ERR_INVALID_ARG;
+  const cudaError_t e = cudaMemcpyToSymbol(g_gemm_wait_ns, &ns, sizeof(ns));
+  if (e != cudaSuccess) {
+    fr_note_cuda_error((int)e);
+    return FR_ERR_CUDA;
+  }
+  return FR_OK;
 }
 
 int fr_gemm_num_configs(void) { return (int)gemm_space().size(); }

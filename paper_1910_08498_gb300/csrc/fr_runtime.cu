@@ -2,6 +2,7 @@
 // the non-blocking dynamic tuner (Sec. 3.2, Sec. 5.3), tuning-cache
 // persistence and the C ABI declared in include/fr.h.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -101,8 +102,18 @@ float otf_inv_pa(double alpha) {
   return alpha > 3.75 ? (float)(1.0 / as_982_host(3.75 / alpha)) : 1.0f;
 }
 
+// host-side fault injection (fr_options.fault_alloc): true for the allocation
+// that is to fail
+bool alloc_fault(fr_ctx *c) {
+  if (c->alloc_countdown <= 0) return false;
+  if (--c->alloc_countdown) return false;
+  c->opt.fault_alloc = 0;  // one shot: a later fr_set_options from fr_get_options does not re-arm it
+  return true;
+}
+
 int ensure_scratch(fr_ctx *c) {
   if (c->scratch) return FR_OK;
+  if (alloc_fault(c)) return FR_ERR_OOM;
   FR_CUDA(cudaMalloc(&c->scratch, c->plane * sizeof(float4)));
   FR_CUDA(cudaMemset(c->scratch, 0, c->plane * sizeof(float4)));
   return FR_OK;
@@ -171,6 +182,7 @@ static int gather_units(fr_ctx *c, const Config &cfg, int n, InsertArgs &a) {
       return FR_OK;
     }
   }
+  if (alloc_fault(c)) return FR_ERR_OOM;
   std::vector<UnitLoad> us;
   int any_split = 0;
   gather_unit_loads(c, cfg.shape, n, 0.0, us, any_split);
@@ -310,6 +322,14 @@ int fr::do_insert_ctx(fr_ctx *c, const void *images, fr_dtype dtype, const float
     if (s.images <= 0) continue;
     const void *img = (const char *)images + (size_t)off * px_bytes;
     const float *r = rot + 9 * (size_t)off;
+    // optional NVTX range per step (debug bit 2); a no-op unless a tool is attached
+    const bool nvtx = (c->opt.debug & 4) != 0;
+    if (nvtx) {
+      char name[96];
+      std::snprintf(name, sizeof(name), "fr_insert S=%d images=%d %s", c->S, s.images,
+                    describe(config_space()[s.config]).c_str());
+      nvtxRangePushA(name);
+    }
     Timing tm = c->tuner.begin(st);
     // host-side fault injection (test hook): report a failed launch, enqueue nothing
     int rc = (c->opt.fault_config > 0 && s.config == c->opt.fault_config - 1)
@@ -321,12 +341,17 @@ int fr::do_insert_ctx(fr_ctx *c, const void *images, fr_dtype dtype, const float
       ks.invalid.insert(s.config);
       int fb = default_config(c);
       rc = run_config(c, fb, img, f16, r, s.images, st);
-      if (rc != FR_OK) { c->tuner.abandon(tm); return rc; }
+      if (rc != FR_OK) {
+        c->tuner.abandon(tm);
+        if (nvtx) nvtxRangePop();
+        return rc;
+      }
       c->tuner.end(tm, ks, fb, s.images, false, st);
       status = FR_ERR_LAUNCH;
     } else {
       c->tuner.end(tm, ks, s.config, s.images, s.tuning, st);
     }
+    if (nvtx) nvtxRangePop();
     ks.last_config = s.config;
     off += s.images;
     ++c->launches;
@@ -548,10 +573,12 @@ int fr_set_options(fr_ctx *c, const fr_options *o) {
     return FR_ERR_INVALID_ARG;
   if (o->forced_config >= (int)config_space().size()) return FR_ERR_INVALID_ARG;
   if (o->fault_config < 0 || o->fault_config > (int)config_space().size()) return FR_ERR_INVALID_ARG;
+  if (o->fault_alloc < 0) return FR_ERR_INVALID_ARG;
   if (o->forced_config >= 0 && !config_valid(c, o->forced_config)) return FR_ERR_UNSUPPORTED;
   bool search_changed = o->search != c->opt.search || o->budget != c->opt.budget ||
                         o->seed != c->opt.seed;
   c->opt = *o;
+  c->alloc_countdown = o->fault_alloc;
   if (search_changed) c->tuner.retune(true);
   return FR_OK;
 }

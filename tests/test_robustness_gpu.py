@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import gemm
 from paper_1910_08498_gb300 import _lib as L
 from paper_1910_08498_gb300 import inputs
 from tests.helpers import TOL_F32, oracle_insert, rel_err
@@ -85,3 +86,77 @@ def test_checkpoint_resume_is_bitwise(where):
         for c in (full, first, second):
             L.fr_destroy(c)
     assert np.array_equal(V1, V2) and np.array_equal(W1, W2)
+
+
+@pytest.mark.parametrize("family", ["scatter", "gather"])
+def test_injected_allocation_failure_falls_back(family):
+    """fr_options.fault_alloc = 1: the first device allocation of the insertion
+    path (the scatter's scratch, or the gather's work-unit list) fails as out of
+    memory; the step is redone with the default configuration (FR_ERR_LAUNCH),
+    every image is inserted once, and the hook disarms itself."""
+    S = 32
+    batches = [inputs.make_batch(S, 90, 150 + b) for b in range(2)]
+    Vr, Wr, _ = oracle_insert(S, batches)
+    ctx = L.fr_create(S)
+    try:
+        cfg = next(i for i in range(L.fr_num_configs())
+                   if L.fr_describe_config(i).startswith(family) and L.fr_config_valid(ctx, i))
+        L.fr_set_options(ctx, tuning=0, forced_config=cfg, fault_alloc=1)
+        s1 = L.fr_insert(ctx, *[t.cuda() for t in batches[0]])
+        s2 = L.fr_insert(ctx, *[t.cuda() for t in batches[1]])
+        armed = L.fr_get_options(ctx).fault_alloc
+        V, W = _finalize(ctx, S)
+    finally:
+        L.fr_destroy(ctx)
+    assert s1 == L.FR_ERR_LAUNCH and s2 == L.FR_OK and armed == 0
+    assert rel_err(V.astype(np.complex128), Vr) <= TOL_F32
+    assert rel_err(W.astype(np.float64), Wr) <= TOL_F32
+
+
+def test_nvtx_ranges_leave_results_unchanged():
+    """fr_options.debug bit 2 (an NVTX range per insertion step) changes no result."""
+    S = 32
+    batches = [inputs.make_batch(S, 70, 160 + b) for b in range(3)]
+    Vr, Wr, _ = oracle_insert(S, batches)
+    ctx = L.fr_create(S)
+    try:
+        L.fr_set_options(ctx, debug=4)
+        st = [L.fr_insert(ctx, *[t.cuda() for t in b]) for b in batches]
+        V, W = _finalize(ctx, S)
+    finally:
+        L.fr_destroy(ctx)
+    assert all(s == L.FR_OK for s in st)
+    assert rel_err(V.astype(np.complex128), Vr) <= TOL_F32
+    assert rel_err(W.astype(np.float64), Wr) <= TOL_F32
+
+
+def test_bulk_gemm_wait_timeout_is_reported_and_recovers():
+    """fr_gemm_set_wait_limit(0): the bulk-copy kernel's waits give up while
+    copies are in flight; the launch reports FR_ERR_TIMEOUT through the status
+    word, ends (after letting its copies land), and the next launch with the
+    default limit computes every instance."""
+    m, n, k, batch = 8, 8, 8, 200000
+    g = torch.Generator(device="cuda").manual_seed(3)
+    A = torch.randn(batch, m, k, device="cuda", generator=g)
+    B = torch.randn(batch, k, n, device="cuda", generator=g)
+    C = torch.empty(batch, m, n, device="cuda")
+    cfg = next(i for i in range(L.fr_gemm_num_configs())
+               if "bulk" in L.fr_gemm_describe_config(i) and L.fr_gemm_config_valid(i, m, n, k))
+    assert L.fr_gemm_device_status() == L.FR_OK
+    L.fr_gemm_set_wait_limit(0)
+    try:
+        L.fr_gemm_run_config(cfg, A, B, C)
+        torch.cuda.synchronize()
+        status = L.fr_gemm_device_status()
+    finally:
+        L.fr_gemm_set_wait_limit(1_000_000_000)
+    assert status == L.FR_ERR_TIMEOUT
+    assert L.fr_gemm_device_status() == L.FR_OK  # read once, cleared
+    C.fill_(float("nan"))
+    L.fr_gemm_run_config(cfg, A, B, C)
+    torch.cuda.synchronize()
+    assert L.fr_gemm_device_status() == L.FR_OK
+    idx = torch.arange(0, batch, 331)
+    As, Bs = A[idx].cpu().numpy(), B[idx].cpu().numpy()
+    err = np.abs(C[idx].cpu().numpy().astype(np.float64) - gemm.bgemm(As, Bs))
+    assert np.all(err <= gemm.fp32_error_bound(As, Bs) + 1e-30)
