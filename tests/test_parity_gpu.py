@@ -104,6 +104,42 @@ def test_every_configuration_matches_oracle_S32(small_ref, cfg):
     assert rel_err(Vs, Vsr) <= TOL_F32 and rel_err(Ws, Wsr) <= TOL_F32
 
 
+@pytest.fixture(scope="module")
+def small_ref_f16(small_ref):
+    img, rot, *_ = small_ref
+    V16, W16, _ = oracle_insert(32, [(img, rot)], f16=True)
+    return V16, W16
+
+
+@pytest.mark.parametrize("cfg", list(range(_num_configs())))
+def test_every_configuration_fp16_images_S32(small_ref, small_ref_f16, cfg):
+    """FP16-stored images through every configuration: within 2e-3 of the
+    oracle fed the FP32 values and within 2e-5 of the oracle fed the
+    FP16-rounded values."""
+    img, rot, Vr, Wr, _ = small_ref
+    V16, W16 = small_ref_f16
+    V, W, _ = gpu_insert(32, [(img, rot)], config=cfg, tuning=False, f16=True)
+    assert rel_err(V, Vr) <= TOL_F16 and rel_err(W, Wr) <= TOL_F16
+    assert rel_err(V, V16) <= TOL_F32 and rel_err(W, W16) <= TOL_F32
+
+
+@pytest.fixture(scope="module")
+def mid_ref():
+    img, rot = inputs.make_batch(128, 48, 21)
+    V, W, _ = oracle_insert(128, [(img, rot)])
+    return img, rot, V, W
+
+
+@pytest.mark.parametrize("cfg", list(range(_num_configs())))
+def test_every_configuration_matches_oracle_S128(mid_ref, cfg):
+    """Every configuration at S = 128 (bricks of every shape span many tiles
+    and a ragged edge of the 129^3 volume), full grid against the oracle."""
+    img, rot, Vr, Wr = mid_ref
+    V, W, _ = gpu_insert(128, [(img, rot)], config=cfg, tuning=False)
+    assert rel_err(V, Vr) <= TOL_F32, (cfg, rel_err(V, Vr), worst(V, Vr, 128))
+    assert rel_err(W, Wr) <= TOL_F32, (cfg, rel_err(W, Wr), worst(W, Wr, 128))
+
+
 def test_gather_is_deterministic(small_ref):
     img, rot, *_ = small_ref
     V1, W1, _ = gpu_insert(32, [(img, rot)], config=1, tuning=False)
