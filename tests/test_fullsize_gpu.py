@@ -109,3 +109,32 @@ def test_largest_image_size_sampled_voxels(cfg):
         L.fr_destroy(ctx)
     assert np.max(np.abs(Vg - Vo)) <= TOL_F32 * scale_v
     assert np.max(np.abs(Wg - Wo)) <= TOL_F32 * scale_w
+
+
+@pytest.mark.parametrize("cfg", [13, -1])
+def test_full_size_whole_grid_small_batch(cfg):
+    """S = 256 with a small batch (40 images): the whole 257^3 grid against
+    the oracle, including the total weight (the sum of the inserted pixels'
+    clipped blob masses, which the oracle's W sums to)."""
+    n = 40
+    img, rot = inputs.make_batch(S, n, 4242)
+    Vr, Wr, _ = oracle.insert(S, img.numpy(), rot.numpy(), a=A32, alpha=ALPHA)
+    ctx = L.fr_create(S, A32, ALPHA, 0, 10000)
+    try:
+        if cfg >= 0 and not L.fr_config_valid(ctx, cfg):
+            pytest.skip("configuration not valid here")
+        L.fr_set_options(ctx, tuning=0, forced_config=cfg)
+        L.fr_insert(ctx, img.cuda(), rot.cuda())
+        D = S + 1
+        V = torch.empty(D ** 3, dtype=torch.complex64, device="cuda")
+        W = torch.empty(D ** 3, dtype=torch.float32, device="cuda")
+        L.fr_finalize(ctx, V, W)
+        torch.cuda.synchronize()
+        assert L.fr_last_device_error(ctx) == L.FR_OK
+        Vg = V.cpu().numpy().astype(np.complex128)
+        Wg = W.cpu().numpy().astype(np.float64)
+    finally:
+        L.fr_destroy(ctx)
+    assert np.max(np.abs(Vg - Vr)) <= TOL_F32 * np.max(np.abs(Vr))
+    assert np.max(np.abs(Wg - Wr)) <= TOL_F32 * np.max(np.abs(Wr))
+    assert abs(Wg.sum() - Wr.sum()) <= 1e-5 * Wr.sum()
