@@ -311,7 +311,7 @@ def run_ours(args):
     # ---- tuning: cold start, exhaustive, non-blocking
     L.fr_reset(ctx)
     L.fr_retune(ctx, True)
-    L.fr_set_options(ctx, tuning=1, search=L.FR_SEARCH_EXHAUSTIVE, steps_per_insert=4, forced_config=-1)
+    L.fr_set_options(ctx, tuning=1, search=L.FR_SEARCH_EXHAUSTIVE, steps_per_insert=0, forced_config=-1)
     tune_inserts = 0
     t_tune = 0.0
     u_tune = 0
@@ -334,7 +334,7 @@ def run_ours(args):
     L.fr_reset(ctx)
     L.fr_retune(ctx, True)
     costmodel.load_pretrained(ctx)
-    L.fr_set_options(ctx, tuning=1, search=L.FR_SEARCH_LEARNED, steps_per_insert=4, forced_config=-1,
+    L.fr_set_options(ctx, tuning=1, search=L.FR_SEARCH_LEARNED, steps_per_insert=0, forced_config=-1,
                      budget=0)
     ln_inserts, t_ln, u_ln = 0, 0.0, 0
     while True:
@@ -708,7 +708,7 @@ def run_stream(L, inputs, costmodel, dev, stream, batches256, updates256, n, f16
             c = L.fr_create(S, 1.9, 15.0, 0, 10000)
             if search == L.FR_SEARCH_LEARNED:
                 costmodel.load_pretrained(c)
-            L.fr_set_options(c, tuning=1, search=search, steps_per_insert=4, budget=0, forced_config=-1)
+            L.fr_set_options(c, tuning=1, search=search, steps_per_insert=0, budget=0, forced_config=-1)
             cs[S] = c
         return cs
 

@@ -97,7 +97,10 @@ typedef struct fr_options {
     int tuning;          /* 1: tune dynamically (default); 0: use the cached best or the default */
     int search;          /* fr_search, default FR_SEARCH_EXHAUSTIVE */
     int budget;          /* configurations to measure per key; 0 = the whole space */
-    int steps_per_insert;/* tuning steps (sub-batches) one fr_insert may take, >= 1 (default 4) */
+    int steps_per_insert;/* tuning steps (sub-batches) one fr_insert may take: >= 1 that many
+                            (at most the configurations left and n); 0 (default): automatic, as
+                            many as keep every step at >= 2e7 estimated voxel updates (about
+                            0.1 ms, so its event timing is accurate), at most 32 */
     int forced_config;   /* >= 0: always use this configuration id; -1 (default): tuner decides */
     uint64_t seed;       /* seed of the search order (default 1) */
     int debug;           /* bit 0: synchronise after every launch and check the device error

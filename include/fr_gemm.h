@@ -71,10 +71,10 @@ int fr_gemm_device_status(void);
 /* Test hook (fault injection from the host): the limit of the bulk-copy
  * kernels' waits for their copies, in ns of the global timer, for launches
  * enqueued after the call (default 1e9).  A wait gives up when a poll finds
- * its copy incomplete ns or more after the wait began, so 0 makes it give up
- * at the first poll that finds a copy still in flight, which exercises the
- * timeout path: the CTA records FR_ERR_TIMEOUT, waits (with the default
- * limit) for its copies in flight and ends; the launch's results are invalid.
+ * its copy incomplete ns or more after the wait began; 0 makes every wait give
+ * up at once, which exercises the timeout path deterministically: the CTA
+ * records FR_ERR_TIMEOUT, waits (with the default limit) for its copies in
+ * flight and ends; the launch's results are invalid.
  * 0 <= ns <= 1e10; synchronous.  FR_ERR_INVALID_ARG or FR_ERR_CUDA on
  * failure. */
 int fr_gemm_set_wait_limit(long long ns);

@@ -331,11 +331,12 @@ __device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // true once the phase with the given parity has completed; false once a poll
-// finds it incomplete limit_ns or more after the start (limit 0: at the first
-// such poll).  Between polls try_wait suspends the thread for a bounded,
-// hardware-defined time.
+// finds it incomplete limit_ns or more after the start, and at once for a
+// limit of 0 (the fault-injection setting).  Between polls try_wait suspends
+// the thread for a bounded, hardware-defined time.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
                                                   long long limit_ns) {
+  if (limit_ns <= 0) return false;
   const unsigned long long t0 = global_ns();
   while (true) {
     if (mbar_test_wait(bar, parity)) return true;

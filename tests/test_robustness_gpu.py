@@ -131,10 +131,10 @@ def test_nvtx_ranges_leave_results_unchanged():
 
 
 def test_bulk_gemm_wait_timeout_is_reported_and_recovers():
-    """fr_gemm_set_wait_limit(0): the bulk-copy kernel's waits give up while
-    copies are in flight; the launch reports FR_ERR_TIMEOUT through the status
-    word, ends (after letting its copies land), and the next launch with the
-    default limit computes every instance."""
+    """fr_gemm_set_wait_limit(0): the bulk-copy kernel's waits give up at once;
+    the launch reports FR_ERR_TIMEOUT through the status word, ends (after
+    letting its copies in flight land), and the next launch with the default
+    limit computes every instance."""
     m, n, k, batch = 8, 8, 8, 200000
     g = torch.Generator(device="cuda").manual_seed(3)
     A = torch.randn(batch, m, k, device="cuda", generator=g)

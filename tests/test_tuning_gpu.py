@@ -111,3 +111,25 @@ def test_adaptive_walks_online(search):
     assert rep["tuned"] == 1 and rep["evaluated"] == 7
     assert rep["best_config"] == min(meas, key=lambda m: m[1])[0]
     assert rel_err(V, Vr) <= TOL_F32 and rel_err(W, Wr) <= TOL_F32
+
+
+def test_automatic_tuning_steps():
+    """steps_per_insert = 0 (the default): an insert takes as many tuning steps
+    as keep each at >= 2e7 estimated voxel updates, at most 32.  S = 128,
+    n = 600: 600 x 128 x 65 x (4/3) pi a^3 / 2e7 = 7.2, so 7 configurations
+    are measured by the first insert; every image is inserted once."""
+    S, n = 128, 600
+    img, rot = inputs.make_batch(S, n, 88)
+    Vr, Wr, _ = oracle_insert(S, [(img, rot)])
+    ctx = L.fr_create(S)
+    try:
+        assert L.fr_get_options(ctx).steps_per_insert == 0
+        L.fr_set_options(ctx, tuning=1, search=L.FR_SEARCH_EXHAUSTIVE)
+        L.fr_insert(ctx, img.cuda(), rot.cuda())
+        torch.cuda.synchronize()
+        rep = L.fr_tuning_report(ctx)
+        V, W = _finalize(ctx, S)
+    finally:
+        L.fr_destroy(ctx)
+    assert rep["evaluated"] == 7
+    assert rel_err(V, Vr) <= TOL_F32 and rel_err(W, Wr) <= TOL_F32
