@@ -50,11 +50,14 @@
 
 namespace fr {
 
-// number of 4-byte fields per kept image in the shared-memory list
-constexpr int LIST_FIELDS = 15;
+// number of 4-byte fields per kept image in the shared-memory list: one
+// 64-byte record per image, the fields grouped by use so that each group is
+// one 16-byte load (plane normal and distance; first in-plane axis and the
+// fractional x; second axis and fractional y; integer centre and image)
+constexpr int LIST_FIELDS = 16;
 enum ListField {
-  LF_E1X, LF_E1Y, LF_E1Z, LF_E2X, LF_E2Y, LF_E2Z, LF_MX, LF_MY, LF_MZ,
-  LF_FX, LF_FY, LF_UZ, LF_CIX, LF_CIY, LF_IMG
+  LF_MX, LF_MY, LF_MZ, LF_UZ, LF_E1X, LF_E1Y, LF_E1Z, LF_FX,
+  LF_E2X, LF_E2Y, LF_E2Z, LF_FY, LF_CIX, LF_CIY, LF_IMG, LF_PAD
 };
 
 // e . c with compensated products and sums (Ogita-Rump-Oishi Dot2), returned
@@ -461,7 +464,7 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
     return;
   }
 
-  float *s_list = reinterpret_cast<float *>(wsmem);      // [LIST_FIELDS][lcap]
+  float *s_list = reinterpret_cast<float *>(__builtin_assume_aligned(wsmem, 16));  // [lcap][LIST_FIELDS]
   float *s_acc = s_list + (size_t)LIST_FIELDS * lcap;   // [3][WV]
   // item queues of 16-bit tags li << 9 | mirrored << 8 | column << 3 | z level
   // (list capacity <= 128): the less shared memory the warps take, the more
@@ -471,8 +474,8 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
   qtag *s_qe = s_qf + QCAP;                              // fast items at the image edge
   qtag *s_qc = s_qe + QCAP;                              // boxes crossing kx = 0
   qtag *s_qd = s_qc + QCAP;                              // voxels in fold columns
-  auto LF = [&](int f, int i) -> float & { return s_list[f * lcap + i]; };
-  auto LI = [&](int f, int i) -> int { return __float_as_int(s_list[f * lcap + i]); };
+  auto LF = [&](int f, int i) -> float & { return s_list[i * LIST_FIELDS + f]; };
+  auto LI = [&](int f, int i) -> int { return __float_as_int(s_list[i * LIST_FIELDS + f]); };
 
   const int split = unit.w & 0xffff, nsplit = (unit.w >> 16) & 0x3fff;
   const bool to_scratch = nsplit > 1 || ((unit.w >> 30) & 1);
