@@ -146,17 +146,22 @@ __device__ __forceinline__ void box_poly_interior(const InsertArgs &args, const 
   const Geom &g = args.g;
   constexpr int ESZ = F16 ? 4 : 8;
   const int row_bytes = g.NX * ESZ;
-  const int step = sgn * ESZ;
-  const int col0 = sgn * kx0 * ESZ;
+  // columns in memory order: the box's columns kx0 .. kx0 + KB - 1 when
+  // direct, the mirrored -(kx0 + KB - 1) .. -kx0 when mirrored; memory column
+  // m is box column j = m (direct) or KB - 1 - m (mirrored), so
+  // dx = fx - j = dx0 + dxs m, and the loads take constant offsets
+  const int cfirst = sgn > 0 ? kx0 : -(kx0 + KB - 1);
+  const float dx0 = sgn > 0 ? fx : fx - (float)(KB - 1);
+  const float dxs = sgn > 0 ? -1.0f : 1.0f;
   // all pixel loads first (they do not depend on the weights), then the math
   float2 px[KB * KB];
 #pragma unroll
   for (int l = 0; l < KB; ++l) {
     int ky = sgn * (ky0 + l);
     ky += ky < 0 ? g.S : 0;
-    const unsigned char *row = ibase + (ky * row_bytes + col0);
+    const unsigned char *row = ibase + (ky * row_bytes + cfirst * ESZ);
 #pragma unroll
-    for (int j = 0; j < KB; ++j) px[l * KB + j] = ld_px<F16>(row + j * step);
+    for (int m = 0; m < KB; ++m) px[l * KB + m] = ld_px<F16>(row + m * ESZ);
   }
   float ar = sr, ai = si, aw = sw;
 #pragma unroll
@@ -165,7 +170,7 @@ __device__ __forceinline__ void box_poly_interior(const InsertArgs &args, const 
     const float ry = fmaf(dy, dy, uz2);
 #pragma unroll
     for (int j = 0; j < KB; ++j) {
-      const float dx = fx - (float)j;
+      const float dx = fmaf(dxs, (float)j, dx0);
       const float r2 = fmaf(dx, dx, ry);
       const float pv = poly_eo(c, fmaf(r2, two_inv_a2, -1.0f));
       const float w = r2 <= g.a2 ? pv : 0.0f;
