@@ -10,8 +10,9 @@
 //  1. cull (A2): one image per lane; an image is kept if its central plane
 //     passes within a + (footprint radius) of the footprint centre and its
 //     extended plane reaches the footprint.  Kept images go, in order, to a
-//     warp-private shared-memory list (structure of arrays) holding the plane
-//     basis and the footprint centre's projection R^T c, formed with error-free
+//     warp-private shared-memory list (one 64-byte record per image, read as
+//     four 16-byte groups) holding the plane basis and the footprint centre's
+//     projection R^T c, formed with error-free
 //     products and split into an integer part and a small remainder so that
 //     in-plane positions keep ~1e-7 absolute accuracy at any |k|;
 //  2. queue: for each list image the warp marks the voxels within a of the
