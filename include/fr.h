@@ -112,7 +112,8 @@ typedef struct fr_options {
     int fault_alloc;     /* test hook (host-side fault injection): k > 0 makes the k-th device
                             allocation the insertion path attempts after this call (work-unit
                             lists, scratch) fail as out of memory; the step then falls back as
-                            for a failed launch.  0 (default): none */
+                            for a failed launch.  One shot: reads back as 0 once it has fired.
+                            0 (default): none */
     int reserved[6];
 } fr_options;
 
