@@ -33,11 +33,19 @@ struct fr_ctx {
   fr::Tuner tuner;
   // gather work-unit lists, keyed by (brick shape, n); most recent first
   struct Units {
-    int shape = -1, n = -1, count = 0, any_split = 0;
+    int shape = -1, n = -1, count = 0, any_split = 0, algo = 0;
     int4 *dev = nullptr;
+    // row-class gather: the per-voxel gather's units over the fold columns
+    // (x <= floor(a)), stored after the main units in dev
+    int fold_count = 0, fold_split = 0;
+    const int4 *fold = nullptr;
   };
   Units units[8];
   unsigned long long *d_phase = nullptr;  // gather phase counters (debug bit 1)
+  // side stream (highest priority) and fork/join events: the row-class
+  // gather's fold-column launch runs beside its main launch
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // cost model
   float *d_mlp = nullptr;
   bool mlp_trained = false;
@@ -57,6 +65,8 @@ int key_bucket(int n);
 InsertArgs base_args(const fr_ctx *c);
 // allocate the context's float4 scratch volume if it has none yet
 int ensure_scratch(fr_ctx *c);
+// create the context's side stream and fork/join events if it has none yet
+int ensure_side_stream(fr_ctx *c);
 // gather work unit with its expected load (images it scans)
 struct UnitLoad {
   double load;
@@ -64,6 +74,11 @@ struct UnitLoad {
 };
 double gather_unit_loads(const fr_ctx *c, int shape, int n, double target,
                          std::vector<UnitLoad> &out, int &any_split);
+// work units of bricks of shape sh tiling x in [x0, x1] (all y, z), split so
+// that no unit exceeds `target` expected images (target <= 0: the total over
+// per_sm units per SM); returns the total expected load
+double brick_unit_loads(const fr_ctx *c, const GatherShape &sh, int x0, int x1, int n,
+                        double target, int per_sm, std::vector<UnitLoad> &out, int &any_split);
 // drop cached batched-insertion plans that refer to c (called by fr_destroy)
 void batched_forget(const fr_ctx *c);
 // release the reconstruction buffers of c (called by fr_destroy)

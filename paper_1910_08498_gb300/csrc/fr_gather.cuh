@@ -436,6 +436,100 @@ __device__ __noinline__ void box_careful(const InsertArgs &args, const float2 *l
   }
 }
 
+// Cull one step of 32 images [cs, cs + 32) ∩ [cs, img1) for a warp footprint
+// centred at (cx, cy, cz) with half extents (hx, hy, hz): one image per lane;
+// an image is kept if its plane passes within a of the footprint box and its
+// extended plane [-H - a, H + a]^2 can reach the footprint (|R^T c| <= ext in
+// plane).  Kept images are appended in order to the warp's list s_list
+// (LIST_FIELDS floats per entry) starting at entry nl, with the centre's
+// projection R^T c formed with compensated products (Dot2) and split into an
+// integer part and a small remainder.  Returns the new list length.
+__device__ __forceinline__ int cull_step(const InsertArgs &args, float *s_list, int nl, int cs,
+                                         int img1, float cx, float cy, float cz, float hx,
+                                         float hy, float hz, float ext, bool any_col) {
+  const int lane = threadIdx.x & 31;
+  const int i = cs + lane;
+  bool keep = false;
+  float e1x = 0, e1y = 0, e1z = 0, e2x = 0, e2y = 0, e2z = 0, mx = 0, my = 0, mz = 0;
+  if (i < img1) {
+    const float *R = args.rot + 9 * (size_t)i;
+    e1x = __ldg(R + 0); e1y = __ldg(R + 3); e1z = __ldg(R + 6);
+    e2x = __ldg(R + 1); e2y = __ldg(R + 4); e2z = __ldg(R + 7);
+    mx = __ldg(R + 2);  my = __ldg(R + 5);  mz = __ldg(R + 8);
+    const float d = mx * cx + my * cy + mz * cz;
+    const float ux = e1x * cx + e1y * cy + e1z * cz;
+    const float uy = e2x * cx + e2y * cy + e2z * cz;
+    // the plane's distance to the footprint box is |d| minus its support
+    const float supp = fabsf(mx) * hx + fabsf(my) * hy + fabsf(mz) * hz;
+    keep = any_col && fabsf(d) <= args.g.a + supp + 1e-3f && fabsf(ux) <= ext && fabsf(uy) <= ext;
+  }
+  const unsigned bal = __ballot_sync(0xffffffffu, keep);
+  if (keep) {
+    const int o = nl + __popc(bal & ((1u << lane) - 1u));
+    float *L = s_list + (size_t)o * LIST_FIELDS;
+    float hxx, lx, hyy, ly, hzz, lz;
+    dot3_dd(e1x, e1y, e1z, cx, cy, cz, hxx, lx);
+    dot3_dd(e2x, e2y, e2z, cx, cy, cz, hyy, ly);
+    dot3_dd(mx, my, mz, cx, cy, cz, hzz, lz);
+    const float rx = rintf(hxx), ry = rintf(hyy);
+    L[LF_E1X] = e1x; L[LF_E1Y] = e1y; L[LF_E1Z] = e1z;
+    L[LF_E2X] = e2x; L[LF_E2Y] = e2y; L[LF_E2Z] = e2z;
+    L[LF_MX] = mx;   L[LF_MY] = my;   L[LF_MZ] = mz;
+    L[LF_FX] = (hxx - rx) + lx;  // hxx - rx is exact
+    L[LF_FY] = (hyy - ry) + ly;
+    L[LF_UZ] = hzz + lz;
+    L[LF_CIX] = __int_as_float((int)rx);
+    L[LF_CIY] = __int_as_float((int)ry);
+    L[LF_IMG] = __int_as_float(i);
+  }
+  return nl + __popc(bal);
+}
+
+// Fold a warp's shared partial sums (s_acc: [3][32 ZC], slot lane * ZC + t for
+// the voxel (fx0 + lane % 8, fy0 + lane / 8, z0 + t)) into HBM and clear them:
+// straight into the double-float accumulators (error-free TwoSum) when the
+// warp is the only writer of its voxels, else into the float4 scratch with
+// atomics (merged after the launch).
+template <int ZC>
+__device__ __forceinline__ void flush_partials(const InsertArgs &args, float *s_acc, int fx0,
+                                               int fy0, int z0, bool to_scratch) {
+  constexpr int WV = 32 * ZC;
+  const Geom &g = args.g;
+  const int lane = threadIdx.x & 31;
+  const int vx = fx0 + (lane & 7), vy = fy0 + (lane >> 3);
+  __syncwarp();
+  if (vx <= g.H && vy <= g.H) {
+#pragma unroll
+    for (int t = 0; t < ZC; ++t) {
+      const int vz = z0 + t;
+      if (vz > g.H) break;
+      const size_t v =
+          ((size_t)(vz + g.H) * g.D + (size_t)(vy + g.H)) * g.NXa + (size_t)(vx - g.xa0);
+      const float ar = s_acc[lane * ZC + t], ai = s_acc[WV + lane * ZC + t],
+                  aw = s_acc[2 * WV + lane * ZC + t];
+      if (aw != 0.f || ar != 0.f || ai != 0.f) {
+        if (!to_scratch) {
+          const float add[3] = {ar, ai, aw};
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            float h = args.acc[c * args.plane + v], l = args.acc[(3 + c) * args.plane + v];
+            dd_add(h, l, add[c]);
+            args.acc[c * args.plane + v] = h;
+            args.acc[(3 + c) * args.plane + v] = l;
+          }
+        } else {
+          atomicAdd(args.scratch + v, make_float4(ar, ai, aw, 0.f));
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < ZC; ++t)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s_acc[c * WV + lane * ZC + t] = 0.f;
+  __syncwarp();
+}
+
 // Per-warp shared memory of the gather: image list, partial sums, item queues.
 __host__ __device__ constexpr size_t gather_warp_smem(int zc, int chunk) {
   return (size_t)LIST_FIELDS * chunk * 4 + (size_t)3 * (32 * zc) * 4 + (size_t)4 * (32 * zc + 32) * 2;
@@ -491,6 +585,8 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
   const int fx0 = g.xa0 + unit.x * BX + wx * 8;
   const int fy0 = -g.H + unit.y * BY + wy * 4;
   const int z0 = -g.H + unit.z * ZC;
+  // the row-class gather leaves the fold columns (x <= floor(a)) to this one
+  if (args.fold_only && fx0 > -g.xa0) return;
   const float cx = fx0 + 3.5f, cy = fy0 + 1.5f, cz = z0 + 0.5f * (ZC - 1);  // footprint centre
   const float hz = 0.5f * (ZC - 1);
   const float rw = sqrtf(3.5f * 3.5f + 1.5f * 1.5f + hz * hz);
@@ -506,8 +602,9 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
   const float ext = reach + rw + 1.0f;
   const int vx = fx0 + (lane & 7), vy = fy0 + (lane >> 3);
   const float dvx = (float)vx - cx, dvy = (float)vy - cy;
-  const bool col_in = vx <= g.H && vy <= g.H;
   const bool fold_col = vx <= -g.xa0;  // x <= floor(a): pixels from both sides of the fold
+  // with fold_only, the columns x > floor(a) belong to the row-class gather
+  const bool col_in = vx <= g.H && vy <= g.H && (!args.fold_only || fold_col);
   const unsigned char *imgs = reinterpret_cast<const unsigned char *>(args.images);
   const size_t img_stride = (size_t)g.S * g.NX * ESZ;
   float2 cpair[POLY_N / 2];
@@ -528,38 +625,8 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
   // straight into the double-float accumulators when this CTA is the only one
   // writing its brick, else into the float4 scratch (merged after the launch)
   auto flush = [&]() {
-    __syncwarp();
     const long long tf = tick();
-    if (col_in) {
-#pragma unroll
-      for (int t = 0; t < ZC; ++t) {
-        const int vz = z0 + t;
-        if (vz > g.H) break;
-        const size_t v =
-            ((size_t)(vz + g.H) * g.D + (size_t)(vy + g.H)) * g.NXa + (size_t)(vx - g.xa0);
-        const float ar = s_acc[lane * ZC + t], ai = s_acc[WV + lane * ZC + t],
-                    aw = s_acc[2 * WV + lane * ZC + t];
-        if (aw != 0.f || ar != 0.f || ai != 0.f) {
-          if (!to_scratch) {
-            const float add[3] = {ar, ai, aw};
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-              float h = args.acc[c * args.plane + v], l = args.acc[(3 + c) * args.plane + v];
-              dd_add(h, l, add[c]);
-              args.acc[c * args.plane + v] = h;
-              args.acc[(3 + c) * args.plane + v] = l;
-            }
-          } else {
-            atomicAdd(args.scratch + v, make_float4(ar, ai, aw, 0.f));
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < ZC; ++t)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) s_acc[c * WV + lane * ZC + t] = 0.f;
-    __syncwarp();
+    flush_partials<ZC>(args, s_acc, fx0, fy0, z0, to_scratch);
     if (prof) ph[PH_FLUSH] += (unsigned long long)(clock64() - tf);
   };
 
@@ -772,7 +839,6 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
     if (qd >= 32 || (all && qd > 0)) drain(s_qd, qd, 3, all);
   };
 
-  const float *rot = args.rot;
   int nl = 0;           // entries in the warp's list
   int since_flush = 0;  // list entries queued since the last flush
   // Cull 32 images per step into the list; when the list is nearly full, or
@@ -783,41 +849,8 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
     if (!last) {
       // ---- cull: one image per lane; kept images go to the warp's list in order
       const long long tc = tick();
-      const int i = cs + lane;
-      bool keep = false;
-      float e1x = 0, e1y = 0, e1z = 0, e2x = 0, e2y = 0, e2z = 0, mx = 0, my = 0, mz = 0;
-      if (i < img1) {
-        const float *R = rot + 9 * (size_t)i;
-        e1x = __ldg(R + 0); e1y = __ldg(R + 3); e1z = __ldg(R + 6);
-        e2x = __ldg(R + 1); e2y = __ldg(R + 4); e2z = __ldg(R + 7);
-        mx = __ldg(R + 2);  my = __ldg(R + 5);  mz = __ldg(R + 8);
-        const float d = mx * cx + my * cy + mz * cz;
-        const float ux = e1x * cx + e1y * cy + e1z * cz;
-        const float uy = e2x * cx + e2y * cy + e2z * cz;
-        // the plane's distance to the footprint box is |d| minus its support
-        const float supp = fabsf(mx) * 3.5f + fabsf(my) * 1.5f + fabsf(mz) * hz;
-        keep = col_in_any(g, fx0, fy0) && fabsf(d) <= a + supp + 1e-3f && fabsf(ux) <= ext &&
-               fabsf(uy) <= ext;
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, keep);
-      if (keep) {
-        const int o = nl + __popc(bal & ((1u << lane) - 1u));
-        float hx, lx, hy, ly, hz2, lz;
-        dot3_dd(e1x, e1y, e1z, cx, cy, cz, hx, lx);
-        dot3_dd(e2x, e2y, e2z, cx, cy, cz, hy, ly);
-        dot3_dd(mx, my, mz, cx, cy, cz, hz2, lz);
-        const float rx = rintf(hx), ry = rintf(hy);
-        LF(LF_E1X, o) = e1x; LF(LF_E1Y, o) = e1y; LF(LF_E1Z, o) = e1z;
-        LF(LF_E2X, o) = e2x; LF(LF_E2Y, o) = e2y; LF(LF_E2Z, o) = e2z;
-        LF(LF_MX, o) = mx;   LF(LF_MY, o) = my;   LF(LF_MZ, o) = mz;
-        LF(LF_FX, o) = (hx - rx) + lx;  // hx - rx is exact
-        LF(LF_FY, o) = (hy - ry) + ly;
-        LF(LF_UZ, o) = hz2 + lz;
-        LF(LF_CIX, o) = __int_as_float((int)rx);
-        LF(LF_CIY, o) = __int_as_float((int)ry);
-        LF(LF_IMG, o) = __int_as_float(i);
-      }
-      nl += __popc(bal);
+      nl = cull_step(args, s_list, nl, cs, img1, cx, cy, cz, 3.5f, 1.5f, hz, ext,
+                     col_in_any(g, fx0, fy0));
       __syncwarp();
       if (prof) ph[PH_CULL] += (unsigned long long)(clock64() - tc);
     }

@@ -1,0 +1,60 @@
+// fr_gather2.cu -- shared-memory sizing, per-device attribute cache and
+// dispatch of the direct-drain gather (fr_gather2.cuh); the kernels are
+// instantiated per brick shape in fr_gather2_s<k>.cu.
+#include <mutex>
+#include <vector>
+
+#include "fr_gather2.cuh"
+
+namespace fr {
+
+// The dynamic shared memory a kernel may use is a per-device attribute:
+// remember, per device and kernel, the size already allowed.
+cudaError_t allow_dynamic_smem(const void *fn, size_t smem) {
+  struct Entry { int dev; const void *fn; size_t smem; };
+  static std::mutex mu;
+  static std::vector<Entry> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  for (const Entry &d : done)
+    if (d.dev == dev && d.fn == fn && d.smem >= smem) return cudaSuccess;
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  // the opt-in limit covers static and dynamic shared memory together
+  if (smem + fa.sharedSizeBytes > (size_t)optin) return cudaErrorInvalidConfiguration;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  for (Entry &d : done)
+    if (d.dev == dev && d.fn == fn) { d.smem = smem; return cudaSuccess; }
+  done.push_back(Entry{dev, fn, smem});
+  return cudaSuccess;
+}
+
+size_t gather2_smem_bytes(const GatherShape &sh, int chunk) {
+  const int nw = sh.bx * sh.by / 32;
+  return (size_t)nw * (sh.zc == 8 ? gather2_warp_smem<8>(chunk) : gather2_warp_smem<4>(chunk));
+}
+
+cudaError_t launch_gather2_shape0(int minw, const InsertArgs &a, cudaStream_t st, int query_only,
+                                  KernelInfo *info);
+cudaError_t launch_gather2_shape1(int minw, const InsertArgs &a, cudaStream_t st, int query_only,
+                                  KernelInfo *info);
+
+cudaError_t launch_gather2(int shape_id, int minw, const InsertArgs &a, cudaStream_t st,
+                           int query_only, KernelInfo *info) {
+  if (a.g.KB != 4 || a.chunk > 64) return cudaErrorInvalidValue;
+  // two-pixel row loads: the images must be 16-byte aligned (fr_insert checks it)
+  if (reinterpret_cast<uintptr_t>(a.images) & 15u) return cudaErrorInvalidValue;
+  switch (shape_id) {
+    case 0: return launch_gather2_shape0(minw, a, st, query_only, info);
+    case 1: return launch_gather2_shape1(minw, a, st, query_only, info);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace fr

@@ -20,7 +20,7 @@ namespace fr {
 // in r^2 held in registers (both on the fly)
 enum WeightMode { W_LUT = 0, W_OTF = 1, W_POLY = 2 };
 constexpr int POLY_N = 12;  // coefficients of the degree-11 weight polynomial
-enum Algo { ALGO_GATHER = 0, ALGO_SCATTER = 1 };
+enum Algo { ALGO_GATHER = 0, ALGO_SCATTER = 1, ALGO_GATHER2 = 2 };
 
 struct Geom {
   int S;      // image side (even)
@@ -50,6 +50,7 @@ struct InsertArgs {
   float inv_i0a;        // 1 / I0(alpha) (on-the-fly weights)
   float inv_pa;         // 1 / (A&S 9.8.2 polynomial at 3.75 / alpha) (on-the-fly weights)
   float poly[POLY_N];   // b as a polynomial in x = 2 r^2 / a^2 - 1, power basis (W_POLY)
+  float2 poly2[POLY_N]; // the same coefficients as pairs (c_k, c_k) for packed FP32x2 FMAs
   int *err;             // device error word
   // gather geometry
   int nbx, nby, nbz;    // bricks per axis
@@ -57,6 +58,7 @@ struct InsertArgs {
   const int4 *units;    // work units: (brick x, y, z, split | nsplit << 16), one per CTA
   int nunits;
   int any_split;        // 1 if some unit shares its brick with other units
+  int fold_only;        // per-voxel gather: only the fold columns (x <= floor(a)); the direct-drain gather takes the rest
   unsigned long long *phase;  // optional per-phase cycle and item counters (PH_*), or null
   // scatter
   float4 *scratch;      // [z][y][x - xa0] (re, im, w, 0)
@@ -89,6 +91,14 @@ struct GatherShape {
 // launchers implemented in the .cu files
 cudaError_t launch_gather(int shape_id, int wmode, const InsertArgs &a, cudaStream_t st,
                           int query_only, KernelInfo *info);
+// direct-drain gather (fr_gather2.cuh): brick shape 0 or 1, register budget
+// for minw (16, 20, 24) resident warps per SM
+cudaError_t launch_gather2(int shape_id, int minw, const InsertArgs &a, cudaStream_t st,
+                           int query_only, KernelInfo *info);
+size_t gather2_smem_bytes(const GatherShape &sh, int chunk);
+// allow a kernel `smem` bytes of dynamic shared memory on the current device
+// (remembered per device and kernel; thread-safe)
+cudaError_t allow_dynamic_smem(const void *fn, size_t smem);
 cudaError_t launch_scatter(int threads, int wmode, const InsertArgs &a, cudaStream_t st,
                            int query_only, KernelInfo *info);
 cudaError_t launch_merge_scratch(const InsertArgs &a, cudaStream_t st);
@@ -107,6 +117,10 @@ cudaError_t launch_debug_blob(const InsertArgs &a, const float *r2, int m, int m
 // number of gather shapes and their geometry
 int num_gather_shapes();
 GatherShape gather_shape(int id);
+// the per-voxel gather over the fold columns only (fold_only set), in bricks
+// of fold_shape() (one 8-column footprint wide), polynomial weights
+GatherShape fold_shape();
+cudaError_t launch_gather_fold(const InsertArgs &a, cudaStream_t st);
 // dynamic shared memory a gather launch needs
 size_t gather_smem_bytes(const GatherShape &sh, int wmode, int lut_n, int chunk);
 size_t gather_persistent_smem_bytes(const GatherShape &sh, int chunk);

@@ -89,7 +89,10 @@ InsertArgs base_args(const fr_ctx *c) {
   a.lut_scale = c->lut_scale;
   a.inv_i0a = c->inv_i0a;
   a.inv_pa = c->inv_pa;
-  for (int k = 0; k < POLY_N; ++k) a.poly[k] = c->poly[k];
+  for (int k = 0; k < POLY_N; ++k) {
+    a.poly[k] = c->poly[k];
+    a.poly2[k] = make_float2(c->poly[k], c->poly[k]);
+  }
   a.err = c->d_err;
   a.scratch = c->scratch;
   a.phase = (c->opt.debug & 2) ? c->d_phase : nullptr;
@@ -111,6 +114,16 @@ bool alloc_fault(fr_ctx *c) {
   return true;
 }
 
+int ensure_side_stream(fr_ctx *c) {
+  if (c->side) return FR_OK;
+  int lo = 0, hi = 0;
+  FR_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  FR_CUDA(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi));
+  FR_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  FR_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  return FR_OK;
+}
+
 int ensure_scratch(fr_ctx *c) {
   if (c->scratch) return FR_OK;
   if (alloc_fault(c)) return FR_ERR_OOM;
@@ -126,11 +139,10 @@ int ensure_scratch(fr_ctx *c) {
 // into several units, each taking a contiguous range of the images.  `target`
 // <= 0 selects the share of one launch of this batch alone (total load over
 // 32 units per SM).  Returns the units with their expected loads, unsorted.
-double gather_unit_loads(const fr_ctx *c, int shape, int n, double target,
-                         std::vector<UnitLoad> &out, int &any_split) {
-  const GatherShape sh = gather_shape(shape);
+double brick_unit_loads(const fr_ctx *c, const GatherShape &sh, int x0, int x1, int n,
+                        double target, int per_sm, std::vector<UnitLoad> &out, int &any_split) {
   const Geom &g = c->g;
-  const int nbx = (g.NXa + sh.bx - 1) / sh.bx, nby = (g.D + sh.by - 1) / sh.by,
+  const int nbx = (x1 - x0 + sh.bx) / sh.bx, nby = (g.D + sh.by - 1) / sh.by,
             nbz = (g.D + sh.zc - 1) / sh.zc;
   const double hx = 0.5 * (sh.bx - 1), hy = 0.5 * (sh.by - 1), hz = 0.5 * (sh.zc - 1);
   const double rb = std::sqrt(hx * hx + hy * hy + hz * hz);
@@ -140,7 +152,7 @@ double gather_unit_loads(const fr_ctx *c, int shape, int n, double target,
   for (int bz = 0; bz < nbz; ++bz)
     for (int by = 0; by < nby; ++by)
       for (int bx = 0; bx < nbx; ++bx) {
-        const double cx = g.xa0 + bx * sh.bx + hx, cy = -g.H + by * sh.by + hy,
+        const double cx = x0 + bx * sh.bx + hx, cy = -g.H + by * sh.by + hy,
                      cz = -g.H + bz * sh.zc + hz;
         const double d = std::sqrt(cx * cx + cy * cy + cz * cz);
         double f = d <= g.a + rb ? 1.0 : (g.a + rb) / d;
@@ -152,7 +164,7 @@ double gather_unit_loads(const fr_ctx *c, int shape, int n, double target,
   if (target <= 0) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    target = std::max(64.0, total / (std::max(sms, 1) * 32.0));
+    target = std::max(64.0, total / (std::max(sms, 1) * (double)per_sm));
   }
   out.clear();
   out.reserve(load.size() + 64);
@@ -170,26 +182,46 @@ double gather_unit_loads(const fr_ctx *c, int shape, int n, double target,
   return total;
 }
 
+double gather_unit_loads(const fr_ctx *c, int shape, int n, double target,
+                         std::vector<UnitLoad> &out, int &any_split) {
+  return brick_unit_loads(c, gather_shape(shape), c->g.xa0, c->g.H, n, target, 32, out,
+                          any_split);
+}
+
 // Work units of a gather launch of this batch alone, heaviest first (so the
 // largest ones start first), cached on the device per (shape, n).
-static int gather_units(fr_ctx *c, const Config &cfg, int n, InsertArgs &a) {
+static int gather_units(fr_ctx *c, const Config &cfg, int n, InsertArgs &a,
+                        const int4 **fold = nullptr, int *nfold = nullptr, int *fold_split = nullptr) {
+  const int algo = cfg.algo == ALGO_GATHER2 ? ALGO_GATHER2 : ALGO_GATHER;
   for (int k = 0; k < 8; ++k) {
     fr_ctx::Units &u = c->units[k];
-    if (u.dev && u.shape == cfg.shape && u.n == n) {
+    if (u.dev && u.shape == cfg.shape && u.n == n && u.algo == algo) {
       a.units = u.dev;
       a.nunits = u.count;
       a.any_split = u.any_split;
+      if (fold) { *fold = u.fold; *nfold = u.fold_count; *fold_split = u.fold_split; }
       return FR_OK;
     }
   }
   if (alloc_fault(c)) return FR_ERR_OOM;
-  std::vector<UnitLoad> us;
-  int any_split = 0;
-  gather_unit_loads(c, cfg.shape, n, 0.0, us, any_split);
-  std::stable_sort(us.begin(), us.end(),
-                   [](const UnitLoad &p, const UnitLoad &q) { return p.load > q.load; });
-  std::vector<int4> host(us.size());
-  for (size_t i = 0; i < us.size(); ++i) host[i] = us[i].unit;
+  std::vector<UnitLoad> us, fs;
+  int any_split = 0, fsplit = 0;
+  if (algo == ALGO_GATHER2) {
+    // the row-class gather's bricks tile x in [floor(a) + 1, H]; the fold
+    // columns x in [-floor(a), floor(a)] go to the per-voxel gather in
+    // bricks one footprint wide, split finely (they are few and heavy)
+    brick_unit_loads(c, gather_shape(cfg.shape), 1 - c->g.xa0, c->g.H, n, 0.0, 32, us, any_split);
+    brick_unit_loads(c, fold_shape(), c->g.xa0, -c->g.xa0, n, 0.0, 8, fs, fsplit);
+  } else {
+    gather_unit_loads(c, cfg.shape, n, 0.0, us, any_split);
+  }
+  auto heavy_first = [](const UnitLoad &p, const UnitLoad &q) { return p.load > q.load; };
+  std::stable_sort(us.begin(), us.end(), heavy_first);
+  std::stable_sort(fs.begin(), fs.end(), heavy_first);
+  std::vector<int4> host;
+  host.reserve(us.size() + fs.size());
+  for (const UnitLoad &x : us) host.push_back(x.unit);
+  for (const UnitLoad &x : fs) host.push_back(x.unit);
   // replace the oldest cached list
   fr_ctx::Units &slot = c->units[7];
   cudaFree(slot.dev);
@@ -199,12 +231,17 @@ static int gather_units(fr_ctx *c, const Config &cfg, int n, InsertArgs &a) {
   FR_CUDA(cudaMalloc(&u.dev, host.size() * sizeof(int4)));
   FR_CUDA(cudaMemcpy(u.dev, host.data(), host.size() * sizeof(int4), cudaMemcpyHostToDevice));
   u.shape = cfg.shape;
+  u.algo = algo;
   u.n = n;
-  u.count = (int)host.size();
+  u.count = (int)us.size();
   u.any_split = any_split;
+  u.fold = u.dev + us.size();
+  u.fold_count = (int)fs.size();
+  u.fold_split = fsplit;
   a.units = u.dev;
   a.nunits = u.count;
   a.any_split = any_split;
+  if (fold) { *fold = u.fold; *nfold = u.fold_count; *fold_split = u.fold_split; }
   return FR_OK;
 }
 
@@ -222,10 +259,16 @@ static void gather_geometry(const fr_ctx *c, const Config &cfg, InsertArgs &a) {
 int prepare_config(fr_ctx *c, int id, int n) {
   const Config &cfg = config_space()[id];
   InsertArgs a = base_args(c);
-  if (cfg.algo == ALGO_GATHER) {
-    int rc = gather_units(c, cfg, n, a);
+  if (cfg.algo == ALGO_GATHER || cfg.algo == ALGO_GATHER2) {
+    const int4 *fold = nullptr;
+    int nfold = 0, fold_split = 0;
+    int rc = gather_units(c, cfg, n, a, &fold, &nfold, &fold_split);
     if (rc) return rc;
-    return a.any_split ? ensure_scratch(c) : FR_OK;
+    if (cfg.algo == ALGO_GATHER2) {
+      rc = ensure_side_stream(c);
+      if (rc) return rc;
+    }
+    return (a.any_split || fold_split) ? ensure_scratch(c) : FR_OK;
   }
   return ensure_scratch(c);
 }
@@ -239,16 +282,40 @@ int run_config(fr_ctx *c, int id, const void *images, int f16, const float *rot,
   a.f16 = f16;
   a.rot = rot;
   a.n = n;
-  if (cfg.algo == ALGO_GATHER) {
+  if (cfg.algo == ALGO_GATHER || cfg.algo == ALGO_GATHER2) {
     gather_geometry(c, cfg, a);
-    int rc = gather_units(c, cfg, n, a);
+    const int4 *fold = nullptr;
+    int nfold = 0, fold_split = 0;
+    int rc = gather_units(c, cfg, n, a, &fold, &nfold, &fold_split);
     if (rc) return rc;
+    if (cfg.algo == ALGO_GATHER2) a.any_split |= fold_split;
     if (a.any_split) {
       rc = ensure_scratch(c);
       if (rc) return rc;
       a.scratch = c->scratch;
     }
-    cudaError_t e = launch_gather(cfg.shape, cfg.wmode, a, st, 0, nullptr);
+    cudaError_t e;
+    if (cfg.algo == ALGO_GATHER2) {
+      // the footprints with fold columns: the per-voxel gather, over those
+      // bricks only, on the side stream so that its few heavy units run
+      // beside the main launch (disjoint voxels; split units add to the
+      // scratch with atomics, merged after both)
+      rc = ensure_side_stream(c);
+      if (rc) return rc;
+      InsertArgs f = a;
+      f.units = fold;
+      f.nunits = nfold;
+      f.fold_only = 1;
+      e = cudaEventRecord(c->ev_fork, st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+      if (e == cudaSuccess) e = launch_gather_fold(f, c->side);
+      if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
+      if (e != cudaSuccess) return cuda_fail(e);
+      e = launch_gather2(cfg.shape, cfg.minw, a, st, 0, nullptr);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, c->ev_join, 0);
+    } else {
+      e = launch_gather(cfg.shape, cfg.wmode, a, st, 0, nullptr);
+    }
     if (e != cudaSuccess) return cuda_fail(e);
     if (a.any_split) {
       e = launch_merge_scratch(a, st);
@@ -287,6 +354,13 @@ int config_valid(const fr_ctx *c, int id) {
   if (cfg.algo == ALGO_GATHER) {
     GatherShape sh = gather_shape(cfg.shape);
     size_t smem = gather_smem_bytes(sh, cfg.wmode, lut_n, cfg.chunk) + 1024;
+    return optin == 0 || (int)smem <= optin;
+  }
+  if (cfg.algo == ALGO_GATHER2) {
+    // 4 x 4 candidate boxes (a < 2) and at least one column inside every box
+    if (c && (c->g.KB != 4 || c->g.H < 4)) return 0;
+    GatherShape sh = gather_shape(cfg.shape);
+    size_t smem = gather2_smem_bytes(sh, cfg.chunk) + 1024;
     return optin == 0 || (int)smem <= optin;
   }
   size_t smem = cfg.wmode == W_LUT ? (size_t)lut_n * sizeof(float2) : 0;
@@ -496,6 +570,9 @@ int fr_destroy(fr_ctx *c) {
   cudaFree(c->d_phase);
   cudaFree(c->d_mlp);
   for (auto &u : c->units) cudaFree(u.dev);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
   delete c;
   return FR_OK;
 }

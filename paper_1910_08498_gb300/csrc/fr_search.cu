@@ -26,11 +26,19 @@ std::vector<std::vector<int>> config_neighbours(const std::vector<int> &valid) {
         int diff = 0;
         if (a.algo == ALGO_GATHER)
           diff = (a.shape != b.shape) + (a.wmode != b.wmode) + (a.chunk != b.chunk);
+        else if (a.algo == ALGO_GATHER2)
+          diff = (a.shape != b.shape) + (a.minw != b.minw);
         else
           diff = (a.threads != b.threads) + (a.wmode != b.wmode) + (a.sub != b.sub);
         adj = diff == 1;
+      } else if (a.algo == ALGO_GATHER2 || b.algo == ALGO_GATHER2) {
+        // the row-class gather neighbours the per-voxel gather of its brick
+        // shape and list capacity with polynomial weights (and nothing else)
+        const Config &g2 = a.algo == ALGO_GATHER2 ? a : b, &o = a.algo == ALGO_GATHER2 ? b : a;
+        adj = o.algo == ALGO_GATHER && o.shape == g2.shape && o.chunk == g2.chunk &&
+              o.wmode == W_POLY && g2.minw == 16;
       } else {
-        adj = a.wmode == b.wmode;
+        adj = a.wmode == b.wmode;  // gather <-> scatter with the same weights
       }
       if (adj) nbr[i].push_back(j);
     }

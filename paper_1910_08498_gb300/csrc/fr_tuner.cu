@@ -34,6 +34,9 @@ const std::vector<Config> &config_space() {
     for (int th : {128, 256})
       for (int w : {W_LUT, W_POLY})
         for (int sub : {256, 1024}) c.push_back(Config{ALGO_SCATTER, -1, w, 0, th, sub});
+    for (int shape : {0, 1})
+      for (int minw : {16, 20, 24})
+        c.push_back(Config{ALGO_GATHER2, shape, W_POLY, 64, 0, 0, minw});
     return c;
   }();
   return v;
@@ -45,6 +48,10 @@ std::string describe(const Config &c) {
     GatherShape s = gather_shape(c.shape);
     std::snprintf(b, sizeof b, "gather bx=%d by=%d zc=%d chunk=%d w=%s", s.bx, s.by, s.zc, c.chunk,
                   c.wmode == W_LUT ? "lut" : c.wmode == W_POLY ? "poly" : "otf");
+  } else if (c.algo == ALGO_GATHER2) {
+    GatherShape s = gather_shape(c.shape);
+    std::snprintf(b, sizeof b, "gather2 bx=%d by=%d zc=%d chunk=%d warps=%d w=poly", s.bx, s.by,
+                  s.zc, c.chunk, c.minw);
   } else {
     std::snprintf(b, sizeof b, "scatter threads=%d sub=%d w=%s", c.threads, c.sub,
                   c.wmode == W_LUT ? "lut" : c.wmode == W_POLY ? "poly" : "otf");
@@ -64,14 +71,15 @@ unsigned long long space_hash() {
 
 void config_features(const Config &c, int S, int n, float a, float *f) {
   for (int i = 0; i < 16; ++i) f[i] = 0.f;
-  f[0] = c.algo == ALGO_SCATTER ? 1.f : 0.f;
-  if (c.algo == ALGO_GATHER) {
+  f[0] = c.algo == ALGO_SCATTER ? 1.f : (c.algo == ALGO_GATHER2 ? 0.5f : 0.f);
+  if (c.algo == ALGO_GATHER || c.algo == ALGO_GATHER2) {
     if (c.shape >= 0 && c.shape < 4) f[1 + c.shape] = 1.f;
     GatherShape s = gather_shape(c.shape);
     f[6] = std::log2((float)c.chunk / 32.f) / 2.f;
     f[13] = s.zc / 8.f;
     f[14] = (float)(s.bx * s.by * s.zc) / 2048.f;
     f[15] = (float)(s.bx * s.by) / 256.f;
+    if (c.algo == ALGO_GATHER2) f[8] = c.minw / 24.f;
   } else {
     f[7] = c.threads / 256.f;
     f[8] = c.sub / 1024.f;

@@ -36,6 +36,7 @@ struct Config {
   int chunk;    // gather: capacity of a warp's shared-memory image list
   int threads;  // scatter: block size
   int sub;      // scatter: images per atomic sub-batch (merged after each)
+  int minw = 0; // direct-drain gather: resident warps per SM the registers allow (16, 20, 24)
 };
 
 const std::vector<Config> &config_space();
