@@ -37,12 +37,23 @@ cudaError_t allow_dynamic_smem(const void *fn, size_t smem) {
 
 size_t gather2_smem_bytes(const GatherShape &sh, int chunk) {
   const int nw = sh.bx * sh.by / 32;
-  return (size_t)nw * (sh.zc == 8 ? gather2_warp_smem<8>(chunk) : gather2_warp_smem<4>(chunk));
+  return (size_t)nw * (sh.zc == 8 ? gather2_warp_smem<8>(chunk) : gather2_warp_smem<16>(chunk));
+}
+
+// brick shapes: columns in x, columns in y, voxels per column (z)
+static const GatherShape kShapes2[] = {{16, 16, 8}, {16, 8, 8}, {16, 8, 16}};
+
+int num_gather2_shapes() { return (int)(sizeof(kShapes2) / sizeof(kShapes2[0])); }
+
+GatherShape gather2_shape(int id) {
+  return id >= 0 && id < num_gather2_shapes() ? kShapes2[id] : GatherShape{0, 0, 0};
 }
 
 cudaError_t launch_gather2_shape0(int minw, const InsertArgs &a, cudaStream_t st, int query_only,
                                   KernelInfo *info);
 cudaError_t launch_gather2_shape1(int minw, const InsertArgs &a, cudaStream_t st, int query_only,
+                                  KernelInfo *info);
+cudaError_t launch_gather2_shape2(int minw, const InsertArgs &a, cudaStream_t st, int query_only,
                                   KernelInfo *info);
 
 cudaError_t launch_gather2(int shape_id, int minw, const InsertArgs &a, cudaStream_t st,
@@ -53,6 +64,7 @@ cudaError_t launch_gather2(int shape_id, int minw, const InsertArgs &a, cudaStre
   switch (shape_id) {
     case 0: return launch_gather2_shape0(minw, a, st, query_only, info);
     case 1: return launch_gather2_shape1(minw, a, st, query_only, info);
+    case 2: return launch_gather2_shape2(minw, a, st, query_only, info);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -10,7 +10,7 @@
 //    levels of its column that lie within a of the plane (u_z is linear in z,
 //    so the run is contiguous) and appends one 16-bit tag per item (list entry,
 //    column, z level) to the warp's tag queue, at lane-major positions found
-//    with one ballot per bit of the run length;
+//    with one ballot per bit of the run length (8- or 16-deep columns);
 //  * evaluation: each full round of 32 tags (one item per lane) forms
 //    u = R^T v from the footprint centre's compensated projection, reflects
 //    u through the origin when it lies in the mirrored half plane (the pixel is
@@ -40,14 +40,19 @@
 
 namespace fr {
 
-constexpr int G2_TCAP = 32 * 8 + 64;  // tags: one list image (<= 32 columns x 8 levels) + < 32 carried over
-constexpr int G2_T2CAP = 64;          // forced second halves: < 32 carried over + <= 32 per round
+constexpr int G2_T2CAP = 64;  // forced second halves: < 32 carried over + <= 32 per round
+
+// tags of one list image (<= 32 columns x ZC levels) + < 32 carried over
+template <int ZC>
+__host__ __device__ constexpr int g2_tcap() {
+  return 32 * ZC + 32;
+}
 
 // Per-warp shared memory: image list, partial sums, tag queues, phase counters.
 template <int ZC>
 __host__ __device__ constexpr size_t gather2_warp_smem(int chunk) {
-  return ((size_t)LIST_FIELDS * chunk * 4 + (size_t)3 * (32 * ZC) * 4 +
-          (size_t)(G2_TCAP + G2_T2CAP) * 2 + (size_t)PH_COUNT * 8 + 15) &
+  return ((size_t)LIST_FIELDS * chunk * 4 + (size_t)3 * (32 * ZC) * 4 + (size_t)G2_T2CAP * 4 +
+          (size_t)g2_tcap<ZC>() * 2 + (size_t)PH_COUNT * 8 + 15) &
          ~(size_t)15;
 }
 
@@ -136,7 +141,7 @@ template <int BX, int BY, int ZC, int F16>
 __device__ __forceinline__ void gather2_warp(const InsertArgs &args, unsigned char *wsmem,
                                              const int4 unit, const int warp) {
   static_assert(BX % 8 == 0 && BY % 4 == 0 && (BX * BY) % 32 == 0, "warp footprint is 8 x 4");
-  static_assert(ZC <= 8, "tags hold 3 bits of z");
+  static_assert(ZC == 8 || ZC == 16, "tags hold 4 bits of z");
   constexpr int WV = 32 * ZC;
   constexpr int ESZ = F16 ? 4 : 8;
   const Geom &g = args.g;
@@ -154,9 +159,9 @@ __device__ __forceinline__ void gather2_warp(const InsertArgs &args, unsigned ch
   }
   float *s_list = reinterpret_cast<float *>(__builtin_assume_aligned(wsmem, 16));
   float *s_acc = s_list + (size_t)LIST_FIELDS * lcap;                               // [3][WV]
-  unsigned short *s_tag = reinterpret_cast<unsigned short *>(s_acc + 3 * WV);       // [G2_TCAP]
-  unsigned short *s_tag2 = s_tag + G2_TCAP;                                         // [G2_T2CAP]
-  unsigned long long *s_ph = reinterpret_cast<unsigned long long *>(s_tag2 + G2_T2CAP);
+  unsigned *s_tag2 = reinterpret_cast<unsigned *>(s_acc + 3 * WV);                  // [G2_T2CAP]
+  unsigned long long *s_ph = reinterpret_cast<unsigned long long *>(s_tag2 + G2_T2CAP);  // [PH_COUNT]
+  unsigned short *s_tag = reinterpret_cast<unsigned short *>(s_ph + PH_COUNT);      // [g2_tcap]
 
   const int split = unit.w & 0xffff, nsplit = (unit.w >> 16) & 0x3fff;
   const bool to_scratch = nsplit > 1 || ((unit.w >> 30) & 1);
@@ -196,13 +201,13 @@ __device__ __forceinline__ void gather2_warp(const InsertArgs &args, unsigned ch
 
   int qt = 0, qt2 = 0;  // queued tags, queued forced second halves
 
-  // One round: lane k evaluates tag q[k] (if k < cnt); an item whose box
-  // crosses kx = 0 queues its other half in s_tag2.
-  auto round = [&](const unsigned short *q, int cnt) {
-    const bool alive = lane < cnt;
-    const unsigned tag = alive ? q[lane] : 0u;
-    const int li = (int)((tag >> 8) & 63), src = (int)((tag >> 3) & 31), t = (int)(tag & 7);
-    const bool forced = ((tag >> 14) & 1u) != 0, fneg = (tag >> 15) != 0;
+  // One round: lane k evaluates tag q[k] (if k < cnt): li << 9 | column << 4 |
+  // z level, plus bit 16 (half forced) and bit 17 (the reflected half) for
+  // the second halves; an item whose box crosses kx = 0 queues its other half
+  // in s_tag2.
+  auto round = [&](unsigned tag, bool alive) {
+    const int li = (int)((tag >> 9) & 63), src = (int)((tag >> 4) & 31), t = (int)(tag & 15);
+    const bool forced = ((tag >> 16) & 1u) != 0, fneg = ((tag >> 17) & 1u) != 0;
     const float *L = s_list + li * LIST_FIELDS;
     const float4 q0 = *reinterpret_cast<const float4 *>(L + LF_MX);   // m, u_z of the centre
     const float4 q1 = *reinterpret_cast<const float4 *>(L + LF_E1X);  // e1, fractional u_x
@@ -225,9 +230,7 @@ __device__ __forceinline__ void gather2_warp(const InsertArgs &args, unsigned ch
     // the box reaches column kx <= 0: the other half as well
     const bool second = valid && !forced && kx0 < 1;
     const unsigned m2 = __ballot_sync(0xffffffffu, second);
-    if (second)
-      s_tag2[qt2 + __popc(m2 & lt)] =
-          (unsigned short)((tag & 0x3fffu) | (1u << 14) | (neg ? 0u : 1u << 15));
+    if (second) s_tag2[qt2 + __popc(m2 & lt)] = (tag & 0xffffu) | (1u << 16) | (neg ? 0u : 1u << 17);
     qt2 += __popc(m2);
     // clamp the box into the stored half plane [0, H] x [-H, H - 1]
     const int kxc = min(max(kx0, 0), g.H - 3);
@@ -255,22 +258,28 @@ __device__ __forceinline__ void gather2_warp(const InsertArgs &args, unsigned ch
     int nr = 0;
     int head = 0;
     for (; qt - head >= 32 || (all && qt > head); head += 32) {
-      round(s_tag + head, qt - head);
+      const bool alive = lane < qt - head;
+      round(alive ? (unsigned)s_tag[head + lane] : 0u, alive);
       ++nr;
       if (qt2 >= 32) {
-        round(s_tag2, 32);
+        const unsigned t2 = s_tag2[lane];
+        __syncwarp();
+        round(t2, true);
         ++nr;
         qt2 -= 32;
-        const unsigned short v = lane < qt2 ? s_tag2[32 + lane] : (unsigned short)0;
+        const unsigned v = lane < qt2 ? s_tag2[32 + lane] : 0u;
         __syncwarp();
         if (lane < qt2) s_tag2[lane] = v;
         __syncwarp();
       }
     }
     if (all && qt2 > 0) {
-      round(s_tag2, qt2);
-      ++nr;
+      const bool alive = lane < qt2;
+      const unsigned t2 = alive ? s_tag2[lane] : 0u;
+      __syncwarp();
       qt2 = 0;
+      round(t2, alive);
+      ++nr;
     }
     const int rest = qt - head < 0 ? 0 : qt - head;
     if (head > 0 && rest) {
@@ -286,7 +295,8 @@ __device__ __forceinline__ void gather2_warp(const InsertArgs &args, unsigned ch
     }
   };
 
-  // generate the items of list entry li (tags at the queue's tail)
+  // generate the items of list entry li (tags at the queue's tail): the run
+  // of z levels t with |u_z(t)| <= a of the lane's column, from u_z linear in t
   auto generate = [&](int li) {
     const long long tq = tick();
     const float *L = s_list + li * LIST_FIELDS;
@@ -299,18 +309,20 @@ __device__ __forceinline__ void gather2_warp(const InsertArgs &args, unsigned ch
     if (!col_in) near = 0;
     const int c = __popc(near);
     const int t0 = near ? __ffs(near) - 1 : 0;
+    const unsigned lt_ = lt;
     int excl = 0, ntag = 0;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
+    for (int b = 0; b < 5; ++b) {
+      if (b == 4 && ZC < 16) break;
       const unsigned bal = __ballot_sync(0xffffffffu, (c >> b) & 1);
-      excl += __popc(bal & lt) << b;
+      excl += __popc(bal & lt_) << b;
       ntag += __popc(bal) << b;
     }
-    const unsigned base = ((unsigned)li << 8) | ((unsigned)lane << 3);
-    const int p0 = qt + excl - t0;
+    const unsigned base = ((unsigned)li << 9) | ((unsigned)lane << 4);
+    const int p0 = qt + excl;
 #pragma unroll
     for (int t = 0; t < ZC; ++t)
-      if ((near >> t) & 1u) s_tag[p0 + t] = (unsigned short)(base | (unsigned)t);
+      if ((near >> t) & 1u) s_tag[p0 + (t - t0)] = (unsigned short)(base | (unsigned)t);
     qt += ntag;
     __syncwarp();
     if (prof && lane == 0) {

@@ -91,8 +91,10 @@ struct GatherShape {
 // launchers implemented in the .cu files
 cudaError_t launch_gather(int shape_id, int wmode, const InsertArgs &a, cudaStream_t st,
                           int query_only, KernelInfo *info);
-// direct-drain gather (fr_gather2.cuh): brick shape 0 or 1, register budget
-// for minw (16, 20, 24) resident warps per SM
+// direct-drain gather (fr_gather2.cuh): brick shape id of gather2_shape(),
+// register budget for minw (16, 20, 24) resident warps per SM
+int num_gather2_shapes();
+GatherShape gather2_shape(int id);
 cudaError_t launch_gather2(int shape_id, int minw, const InsertArgs &a, cudaStream_t st,
                            int query_only, KernelInfo *info);
 size_t gather2_smem_bytes(const GatherShape &sh, int chunk);

@@ -210,7 +210,7 @@ static int gather_units(fr_ctx *c, const Config &cfg, int n, InsertArgs &a,
     // the row-class gather's bricks tile x in [floor(a) + 1, H]; the fold
     // columns x in [-floor(a), floor(a)] go to the per-voxel gather in
     // bricks one footprint wide, split finely (they are few and heavy)
-    brick_unit_loads(c, gather_shape(cfg.shape), 1 - c->g.xa0, c->g.H, n, 0.0, 32, us, any_split);
+    brick_unit_loads(c, gather2_shape(cfg.shape), 1 - c->g.xa0, c->g.H, n, 0.0, 32, us, any_split);
     brick_unit_loads(c, fold_shape(), c->g.xa0, -c->g.xa0, n, 0.0, 8, fs, fsplit);
   } else {
     gather_unit_loads(c, cfg.shape, n, 0.0, us, any_split);
@@ -247,7 +247,7 @@ static int gather_units(fr_ctx *c, const Config &cfg, int n, InsertArgs &a,
 
 // Fill the launch geometry of configuration `cfg` into `a`.
 static void gather_geometry(const fr_ctx *c, const Config &cfg, InsertArgs &a) {
-  GatherShape sh = gather_shape(cfg.shape);
+  GatherShape sh = cfg.algo == ALGO_GATHER2 ? gather2_shape(cfg.shape) : gather_shape(cfg.shape);
   a.chunk = cfg.chunk;
   a.nbx = (c->g.NXa + sh.bx - 1) / sh.bx;
   a.nby = (c->g.D + sh.by - 1) / sh.by;
@@ -359,7 +359,7 @@ int config_valid(const fr_ctx *c, int id) {
   if (cfg.algo == ALGO_GATHER2) {
     // 4 x 4 candidate boxes (a < 2) and at least one column inside every box
     if (c && (c->g.KB != 4 || c->g.H < 4)) return 0;
-    GatherShape sh = gather_shape(cfg.shape);
+    GatherShape sh = gather2_shape(cfg.shape);
     size_t smem = gather2_smem_bytes(sh, cfg.chunk) + 1024;
     return optin == 0 || (int)smem <= optin;
   }

@@ -34,9 +34,10 @@ const std::vector<Config> &config_space() {
     for (int th : {128, 256})
       for (int w : {W_LUT, W_POLY})
         for (int sub : {256, 1024}) c.push_back(Config{ALGO_SCATTER, -1, w, 0, th, sub});
-    for (int shape : {0, 1})
+    for (int shape = 0; shape < num_gather2_shapes(); ++shape)
       for (int minw : {16, 20, 24})
         c.push_back(Config{ALGO_GATHER2, shape, W_POLY, 64, 0, 0, minw});
+    for (int minw : {20, 24}) c.push_back(Config{ALGO_GATHER2, 2, W_POLY, 32, 0, 0, minw});
     return c;
   }();
   return v;
@@ -49,7 +50,7 @@ std::string describe(const Config &c) {
     std::snprintf(b, sizeof b, "gather bx=%d by=%d zc=%d chunk=%d w=%s", s.bx, s.by, s.zc, c.chunk,
                   c.wmode == W_LUT ? "lut" : c.wmode == W_POLY ? "poly" : "otf");
   } else if (c.algo == ALGO_GATHER2) {
-    GatherShape s = gather_shape(c.shape);
+    GatherShape s = gather2_shape(c.shape);
     std::snprintf(b, sizeof b, "gather2 bx=%d by=%d zc=%d chunk=%d warps=%d w=poly", s.bx, s.by,
                   s.zc, c.chunk, c.minw);
   } else {
@@ -73,10 +74,10 @@ void config_features(const Config &c, int S, int n, float a, float *f) {
   for (int i = 0; i < 16; ++i) f[i] = 0.f;
   f[0] = c.algo == ALGO_SCATTER ? 1.f : (c.algo == ALGO_GATHER2 ? 0.5f : 0.f);
   if (c.algo == ALGO_GATHER || c.algo == ALGO_GATHER2) {
-    if (c.shape >= 0 && c.shape < 4) f[1 + c.shape] = 1.f;
-    GatherShape s = gather_shape(c.shape);
+    if (c.algo == ALGO_GATHER && c.shape >= 0 && c.shape < 4) f[1 + c.shape] = 1.f;
+    GatherShape s = c.algo == ALGO_GATHER2 ? gather2_shape(c.shape) : gather_shape(c.shape);
     f[6] = std::log2((float)c.chunk / 32.f) / 2.f;
-    f[13] = s.zc / 8.f;
+    f[13] = s.zc / 16.f;
     f[14] = (float)(s.bx * s.by * s.zc) / 2048.f;
     f[15] = (float)(s.bx * s.by) / 256.f;
     if (c.algo == ALGO_GATHER2) f[8] = c.minw / 24.f;

@@ -68,13 +68,13 @@ def test_relative_performance_consistent_with_invocations(lib):
 
 def test_configuration_space(lib):
     n = L.fr_num_configs()
-    assert n == 50
+    assert n == 55
     descs = [L.fr_describe_config(i) for i in range(n)]
     assert len(set(descs)) == n
     assert sum(d.startswith("gather ") for d in descs) == 36
-    assert sum(d.startswith("gather2 ") for d in descs) == 6
+    assert sum(d.startswith("gather2 ") for d in descs) == 11
     assert sum("w=otf" in d for d in descs) == 12
-    assert sum("w=poly" in d for d in descs) == 22
+    assert sum("w=poly" in d for d in descs) == 27
     with pytest.raises(L.FrError):
         L.fr_describe_config(n)
 
