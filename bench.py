@@ -187,8 +187,28 @@ def barrier(world):
 
 # ------------------------------------------------------------------ CPU oracle timing
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
 def oracle_sample(S, img_cpu, rot_cpu, target_s, a):
-    """Time the FP64 oracle on the first m images, m sized for ~target_s of work."""
+    """Time the FP64 oracle on the first m images, m sized for ~target_s of
+    work, on every host core; and on one core, on a sample sized for about a
+    sixth of that time."""
     import oracle
     oracle.build()
     nt = oracle.max_threads()
@@ -200,9 +220,62 @@ def oracle_sample(S, img_cpu, rot_cpu, target_s, a):
     t1 = time.perf_counter()
     _, _, c = oracle.insert(S, img_cpu[:m], rot_cpu[:m], a=a, alpha=15.0, nthreads=nt)
     dt = time.perf_counter() - t1
+    # one thread: a sample of m1 images sized from the parallel rate
+    m1 = int(max(1, min(m, m * target_s / 6.0 / max(dt * nt, 1e-3))))
+    t2 = time.perf_counter()
+    _, _, c1 = oracle.insert(S, img_cpu[:m1], rot_cpu[:m1], a=a, alpha=15.0, nthreads=1)
+    dt1 = time.perf_counter() - t2
     return {"value": c / dt, "unit": UNIT, "cores": nt, "kind": "oracle",
+            "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+            "single_thread": {"value": c1 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"first {m1} images of batch 0 ({c1} updates, {dt1:.1f} s)"},
             "sample": f"first {m} images of batch 0 ({c} updates, {dt:.1f} s, FP64 scatter, OpenMP z-slab "
                       f"ownership, {nt} threads)"}
+
+
+# ------------------------------------------------------------------ precision (error vs the FP64 oracle)
+
+TOL_F32, TOL_F16 = 2e-5, 2e-3
+
+
+def sample_voxels(S, seed, k):
+    """k voxel coordinates of an (S+1)^3 volume: the centre and its
+    neighbourhood (many planes meet there), the fold columns, and random."""
+    import numpy as np
+    H = S // 2
+    rng = np.random.default_rng(seed)
+    pts = [(0, 0, 0), (1, 0, 0), (-1, 0, 1), (2, -3, 1)]
+    pts += [tuple(int(v) for v in rng.integers(-6, 7, 3)) for _ in range(max(0, k // 4))]
+    pts += [(int(rng.integers(-1, 2)), int(rng.integers(-H, H + 1)), int(rng.integers(-H, H + 1)))
+            for _ in range(max(0, k // 4))]
+    while len(pts) < k:
+        pts.append((int(rng.integers(-1, H + 1)), int(rng.integers(-H, H + 1)),
+                    int(rng.integers(-H, H + 1))))
+    return pts[:k]
+
+
+def gpu_samples(L, ctx, S, pts, dev):
+    """Finalize ctx and read V, W at pts with the grid maxima of |V| and W."""
+    import numpy as np
+    import torch
+    D, H = S + 1, S // 2
+    V = torch.empty(D ** 3, dtype=torch.complex64, device=dev)
+    W = torch.empty(D ** 3, dtype=torch.float32, device=dev)
+    L.fr_finalize(ctx, V, W)
+    idx = torch.tensor([((z + H) * D + (y + H)) * D + (x + H) for x, y, z in pts], device=dev)
+    out = {"pts": pts, "V": V[idx].cpu().numpy().astype(np.complex128),
+           "W": W[idx].cpu().numpy().astype(np.float64),
+           "scale_v": V.abs().max().item(), "scale_w": W.max().item()}
+    del V, W
+    return out
+
+
+def sample_errors(g, Vo, Wo):
+    """err_V, err_W of sampled GPU values against the oracle's, relative to
+    the grid maxima of |V| and W."""
+    import numpy as np
+    return {"err_V": float(np.max(np.abs(g["V"] - Vo)) / g["scale_v"]),
+            "err_W": float(np.max(np.abs(g["W"] - Wo)) / g["scale_w"]), "voxels": len(g["pts"])}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -244,6 +317,7 @@ def run_reference(args):
             "config": {"workload": workload_name(S, n, args.dtype), "S": S, "n_per_step": m,
                        "parallelism": "host threads"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": nt, "kind": "oracle",
+                             "nproc": os.cpu_count(), "cpu_model": cpu_model(),
                              "sample": f"{m} images per step (of a {n}-image batch), FP64 scatter"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -366,6 +440,17 @@ def run_ours(args):
     u_all = sum_over_ranks(u_tu, world, dev)
     value = u_all / t_tu_max
     rep_tuned = L.fr_tuning_report(ctx)
+
+    # ---- precision of the timed configuration: batch 0 alone into a fresh
+    # context, sampled voxels (compared with the FP64 oracle in the
+    # cpu_baseline leg, after the timed regions)
+    prec_pts = sample_voxels(S, 11, 32)
+    prec_gpu = {}
+    ctxp = L.fr_create(S, a, 15.0, 0, 10000)
+    L.fr_set_options(ctxp, tuning=0, forced_config=best)
+    L.fr_insert(ctxp, *batches[0])
+    prec_gpu["f32" if not f16 else "f16"] = gpu_samples(L, ctxp, S, prec_pts, dev)
+    L.fr_destroy(ctxp)
 
     # ---- e2e: pinned host inputs copied in every step
     e2e = None
@@ -537,6 +622,9 @@ def run_ours(args):
         t16 = e0.elapsed_time(e1) / 1e3
         fp16 = {"value": sum(updates[i % 2] for i in range(args.steps)) / t16, "unit": UNIT,
                 "config": L.fr_describe_config(best), "ms_per_step": 1e3 * t16 / args.steps}
+        L.fr_reset(ctx16)
+        L.fr_insert(ctx16, *h16[0])
+        prec_gpu["f16"] = gpu_samples(L, ctx16, S, prec_pts, dev)
         L.fr_destroy(ctx16)
         del h16
 
@@ -550,15 +638,18 @@ def run_ours(args):
         gemm_dyn = run_gemm_dynamic(L, dev, stream)
 
     batched = None
+    c3_samples = None
     if not args.no_batched:
-        batched = run_batched(L, inputs, dev, stream, max(2, args.steps // 3), 1, f16)
+        batched, c3_samples = run_batched(L, inputs, dev, stream, max(2, args.steps // 3), 1, f16)
 
     cpu = None
+    precision = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         img0, rot0 = batches[0]
         m = min(n, 2000)
         imgc = (inputs.half_values(img0[:m]) if f16 else img0[:m]).cpu().numpy()
         cpu = oracle_sample(S, imgc, rot0[:m].cpu().numpy(), args.cpu_seconds, a)
+        precision = run_precision(prec_gpu, batches[0], S, a, f16, c3_samples, dev, inputs)
 
     rep = rep_tune
     line = {
@@ -593,6 +684,7 @@ def run_ours(args):
                                 / (20 * t_tu / args.steps) - 1.0) if ln_inserts <= 20 else None},
         "roofline": roof,
         "cpu_baseline": cpu,
+        "precision": precision,
         "e2e": e2e,
         "fp16": fp16,
         "reconstruct": recon,
@@ -600,7 +692,7 @@ def run_ours(args):
         "stream": stream_exp,
         "batched": batched,
         "gemm_dynamic": gemm_dyn,
-        "gpu_launches": args.steps * launches_per_insert(L, best, n),
+        "gpu_launches": args.steps * launches_per_insert(L, ctx, best, n),
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"], "reasons": clocks["reasons"]},
         "wall_s_timed": wall,
     }
@@ -657,12 +749,66 @@ def run_batched(L, inputs, dev, stream, steps, warmup, f16):
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3 / steps
         out[name] = {"value": ups / t, "ms_per_pass": 1e3 * t}
+    # one persistent pass into cleared volumes, sampled per batch (compared
+    # with the FP64 oracle in the cpu_baseline leg)
+    for c in ctx_p:
+        L.fr_reset(c)
+    persistent(1)
+    samples = []
+    for b, ((S, n, seed), c) in enumerate(zip(spec, ctx_p)):
+        samples.append(((S, n, seed), gpu_samples(L, c, S, sample_voxels(S, 100 + b, 6), dev)))
     for c in ctx_p + ctx_s:
         L.fr_destroy(c)
     sizes = sorted({S for S, _, _ in spec})
-    return {"workload": f"{len(spec)} batches, S in {sizes}, n in [500, 5000] (seeded), one volume each, "
-                        f"{'FP16' if f16 else 'FP32'} images",
-            "updates_per_pass": ups, "images_per_pass": sum(n for _, n, _ in spec), **out}
+    return ({"workload": f"{len(spec)} batches, S in {sizes}, n in [500, 5000] (seeded), one volume each, "
+                         f"{'FP16' if f16 else 'FP32'} images",
+             "updates_per_pass": ups, "images_per_pass": sum(n for _, n, _ in spec), **out},
+            {"f16": f16, "batches": samples})
+
+
+def run_precision(prec_gpu, batch0, S, a, f16_run, c3, dev, inputs):
+    """The error of the timed configurations against the FP64 oracle, on
+    sampled voxels the oracle computes one by one: the S = 256 batch (FP32
+    images; FP16 images against the oracle fed the FP32 values and the
+    FP16-rounded values) and every batch of the uneven-batch workload."""
+    import torch
+    import oracle
+    oracle.build()
+    img0, rot0 = batch0
+    rot = rot0.cpu().numpy()
+    pts = next(iter(prec_gpu.values()))["pts"]
+    vals = (inputs.half_values(img0) if f16_run else img0).cpu().numpy()
+    Vo, Wo = oracle.voxels(S, vals, rot, pts, a=a, alpha=15.0)
+    out = {"bounds": {"f32": TOL_F32, "f16": TOL_F16},
+           "note": "err = max over sampled voxels of |GPU - FP64 oracle| / max over the grid "
+                   "(|V| or W); centre, fold columns and random voxels"}
+    if "f32" in prec_gpu:
+        out["f32"] = sample_errors(prec_gpu["f32"], Vo, Wo)
+    if "f16" in prec_gpu:
+        if f16_run:
+            out["f16"] = {"vs_f16_values": sample_errors(prec_gpu["f16"], Vo, Wo)}
+        else:
+            Vh, Wh = oracle.voxels(S, inputs.half_values(inputs.to_half(img0)).cpu().numpy(), rot,
+                                   pts, a=a, alpha=15.0)
+            out["f16"] = {"vs_f32_values": sample_errors(prec_gpu["f16"], Vo, Wo),
+                          "vs_f16_values": sample_errors(prec_gpu["f16"], Vh, Wh)}
+    if c3:
+        per = []
+        for (Sb, n, seed), g in c3["batches"]:
+            gen = torch.Generator(device=dev)
+            gen.manual_seed(seed)
+            rb = inputs.random_rotations(n, gen, dev)
+            ib = inputs.random_images(Sb, n, gen, dev)
+            if c3["f16"]:
+                ib = inputs.half_values(inputs.to_half(ib))
+            Vb, Wb = oracle.voxels(Sb, ib.cpu().numpy(), rb.cpu().numpy(), g["pts"], a=a, alpha=15.0)
+            e = sample_errors(g, Vb, Wb)
+            per.append({"S": Sb, "n": n, "err_V": e["err_V"], "err_W": e["err_W"]})
+            del ib, rb
+        out["c3"] = {"images": "FP16 (vs the FP16-rounded values)" if c3["f16"] else "FP32",
+                     "batches": len(per), "max_err_V": max(p["err_V"] for p in per),
+                     "max_err_W": max(p["err_W"] for p in per), "per_batch": per}
+    return out
 
 
 def run_stream(L, inputs, costmodel, dev, stream, batches256, updates256, n, f16, seed):
@@ -813,16 +959,15 @@ def run_gemm_dynamic(L, dev, stream, sizes=10, calls=100, seed=7, target_bytes=5
             "hbm_gbs": peak, "hbm_source": src}
 
 
-def launches_per_insert(L, cfg, n):
-    d = L.fr_describe_config(cfg)
-    if d.startswith("gather"):
-        return 1
-    sub = int(d.split("sub=")[1].split()[0])
-    return 2 * math.ceil(n / sub)  # scatter + merge per sub-batch
+def launches_per_insert(L, ctx, cfg, n):
+    """Kernel launches of one insert of n images with configuration cfg (one
+    step: tuning is off in the timed region)."""
+    return L.fr_insert_launches(ctx, cfg, n)
 
 
 GATHER_SOURCES = ("fr_device.cuh", "fr_gather.cuh", "fr_gather_common.cu", "fr_gather_launch.inc",
-                  "fr_gather_shapes.h", "fr_internal.h")
+                  "fr_gather_shapes.h", "fr_internal.h", "fr_gather2.cuh", "fr_gather2.cu",
+                  "fr_gather2_launch.inc")
 
 
 def source_hash():
@@ -832,7 +977,8 @@ def source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1910_08498_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f in GATHER_SOURCES or (f.startswith("fr_gather_s") and f.endswith(".cu")):
+        if f in GATHER_SOURCES or ((f.startswith("fr_gather_s") or f.startswith("fr_gather2_s"))
+                                   and f.endswith(".cu")):
             h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -931,8 +1077,8 @@ def main():
         from paper_1910_08498_gb300 import inputs
         dev = torch.device("cuda", 0)
         L.lib()
-        res = run_batched(L, inputs, dev, torch.cuda.current_stream(), args.steps, args.warmup,
-                          args.dtype == "f16")
+        res, _ = run_batched(L, inputs, dev, torch.cuda.current_stream(), args.steps, args.warmup,
+                             args.dtype == "f16")
         print(json.dumps(res), flush=True)
         return 0
     if args.impl == "reference":

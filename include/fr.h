@@ -272,6 +272,13 @@ int fr_config_valid(const fr_ctx *ctx, int id);
  * S, n, a).  Host function. */
 int fr_config_features(int id, int S, int n, float a, float *out16);
 
+/* Number of kernel launches one insertion step of n images with
+ * configuration id enqueues (*out): the insertion kernels plus the scratch
+ * merges.  Builds the configuration's work units if needed (host work and a
+ * small device upload, as the first insert with it would); enqueues no
+ * kernel.  FR_ERR_INVALID_ARG for a bad id, n < 1 or a null out. */
+int fr_insert_launches(fr_ctx *ctx, int id, int n, int *out);
+
 /* ---------------------------------------------------------------- measurement */
 
 /* Exact number of (pixel, voxel) updates that inserting images with these

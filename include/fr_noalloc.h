@@ -2,10 +2,10 @@
  * fr_noalloc.h -- insertion entry point that allocates no device memory.
  *
  * The paper has no counterpart of this call: it is a service entry point of
- * this library.  It runs the same insertion (the step of Algorithm 1,
- * Sec. 5.3.1, with the definition written out at the top of fr.h) through
- * the atomic scatter kernel, whose scratch volume is a fixed array in the
- * library's static device memory instead of a cudaMalloc'd buffer.
+ * this library.  It runs the same insertion as fr_insert (the definition is
+ * written out in fr.h) through the atomic scatter kernel, whose scratch
+ * volume is a fixed array in the library's static device memory instead of a
+ * cudaMalloc'd buffer.
  *
  * Who needs it: callers that must not enter the device allocator for the
  * duration of the call.  cudaMalloc and cudaFree can synchronise the device
@@ -64,6 +64,12 @@ extern "C" {
  * library's device code on that device if lazy loading has not done so yet)
  * while that device is current, and caches it.  Make that first call before
  * any stream capture begins.
+ *
+ * The batch is added in sub-batches of 1024 images, each merged into V and W
+ * before the next: if a launch fails part way (FR_ERR_CUDA), the sub-batches
+ * before it have been added and the rest have not, so V and W are then
+ * unspecified and must be rebuilt from zero.  The argument checks all come
+ * before any device work: every other error leaves V and W untouched.
  *
  * Returns FR_OK, FR_ERR_INVALID_ARG (null pointer, misaligned images, n or a
  * or alpha out of range, bad dtype), FR_ERR_UNSUPPORTED, FR_ERR_NOALLOC_LIMIT,

@@ -104,6 +104,7 @@ def _lib():
             "fr_num_configs": (i, []),
             "fr_describe_config": (i, [i, ctypes.c_char_p, i]),
             "fr_config_valid": (i, [vp, i]),
+            "fr_insert_launches": (i, [vp, i, i, P(i)]),
             "fr_config_features": (i, [i, i, i, f, P(f)]),
             "fr_count_updates": (i, [vp, vp, i, vp, P(ctypes.c_ulonglong)]),
             "fr_relative_performance": (d, [d, d, d, d]),
@@ -354,6 +355,13 @@ def fr_describe_config(i: int) -> str:
 
 def fr_config_valid(ctx, i: int) -> bool:
     return bool(_lib().fr_config_valid(ctx, i))
+
+
+def fr_insert_launches(ctx, i: int, n: int) -> int:
+    """Kernel launches of one insertion step of n images with configuration i."""
+    out = ctypes.c_int(0)
+    _check(_lib().fr_insert_launches(ctx, int(i), int(n), ctypes.byref(out)), "fr_insert_launches")
+    return out.value
 
 
 def fr_config_features(i: int, S: int, n: int, a: float):

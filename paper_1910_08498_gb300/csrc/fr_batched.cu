@@ -76,7 +76,7 @@ int batched_config(fr_ctx *c, int n, int dtype) {
   TuneKey k{c->S, key_bucket(n), c->g.a, dtype};
   int best = c->tuner.best_for(k);
   if (c->opt.forced_config >= 0) best = c->opt.forced_config;
-  if (best < 0 || config_space()[best].algo != ALGO_GATHER) best = default_config(c);
+  if (best < 0 || config_space()[best].algo != ALGO_GATHER) best = default_gather_config(c);
   return best;
 }
 

@@ -10,7 +10,7 @@ namespace fr {
 
 // The dynamic shared memory a kernel may use is a per-device attribute:
 // remember, per device and kernel, the size already allowed.
-cudaError_t allow_dynamic_smem(const void *fn, size_t smem) {
+cudaError_t allow_dynamic_smem(const void *fn, size_t smem, int carveout) {
   struct Entry { int dev; const void *fn; size_t smem; };
   static std::mutex mu;
   static std::vector<Entry> done;
@@ -28,11 +28,47 @@ cudaError_t allow_dynamic_smem(const void *fn, size_t smem) {
   // the opt-in limit covers static and dynamic shared memory together
   if (smem + fa.sharedSizeBytes > (size_t)optin) return cudaErrorInvalidConfiguration;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess && carveout >= 0)
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
   if (e != cudaSuccess) return e;
   for (Entry &d : done)
     if (d.dev == dev && d.fn == fn) { d.smem = smem; return cudaSuccess; }
   done.push_back(Entry{dev, fn, smem});
   return cudaSuccess;
+}
+
+int device_sm_count() {
+  static std::mutex mu;
+  static std::vector<int> n;  // by device ordinal
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)n.size() <= dev) n.resize(dev + 1, 0);
+  if (n[dev] <= 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    n[dev] = v > 0 ? v : 1;
+  }
+  return n[dev];
+}
+
+int resident_ctas(const void *fn, int threads, size_t smem) {
+  struct Entry { int dev; const void *fn; int threads; size_t smem; int ctas; };
+  static std::mutex mu;
+  static std::vector<Entry> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (const Entry &d : done)
+      if (d.dev == dev && d.fn == fn && d.threads == threads && d.smem == smem) return d.ctas;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess)
+    return 0;
+  std::lock_guard<std::mutex> lk(mu);
+  done.push_back(Entry{dev, fn, threads, smem, per_sm});
+  return per_sm;
 }
 
 size_t gather2_smem_bytes(const GatherShape &sh, int chunk) {

@@ -590,20 +590,10 @@ cudaError_t launch_bulk(const GemmConfig &c, int m, int n, int k, const float *A
   int threads = 0;
   if (!bulk_plan(c, m, n, k, batch, &g, &smem, &threads)) return cudaErrorInvalidValue;
   auto fn = bgemm_bulk_kernel<TY, TX>;
-  static std::once_flag once;
-  static cudaError_t attr = cudaSuccess;
-  std::call_once(once, [&] {
-    attr = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BULK_SMEM_MAX);
-    if (attr == cudaSuccess)
-      attr = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                  cudaSharedmemCarveoutMaxShared);
-  });
-  if (attr != cudaSuccess) return attr;
-  int per_sm = 0, dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+  cudaError_t e = allow_dynamic_smem((const void *)fn, BULK_SMEM_MAX, cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
+  const int sms = device_sm_count();
+  const int per_sm = resident_ctas((const void *)fn, threads, smem);
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const long long grid = std::min<long long>(g.groups, (long long)per_sm * sms);
   fn<<<(unsigned)grid, threads, smem, st>>>(g, A, B, C);

@@ -99,8 +99,15 @@ cudaError_t launch_gather2(int shape_id, int minw, const InsertArgs &a, cudaStre
                            int query_only, KernelInfo *info);
 size_t gather2_smem_bytes(const GatherShape &sh, int chunk);
 // allow a kernel `smem` bytes of dynamic shared memory on the current device
-// (remembered per device and kernel; thread-safe)
-cudaError_t allow_dynamic_smem(const void *fn, size_t smem);
+// (and, if carveout >= 0, set its preferred shared-memory carveout in percent);
+// remembered per device and kernel; thread-safe
+cudaError_t allow_dynamic_smem(const void *fn, size_t smem, int carveout = -1);
+// SM count of the current device (cached per device; thread-safe)
+int device_sm_count();
+// resident CTAs per SM of kernel fn with `threads` threads and `smem` bytes
+// of dynamic shared memory on the current device (cached per device, kernel
+// and size; thread-safe); 0 if it cannot run
+int resident_ctas(const void *fn, int threads, size_t smem);
 cudaError_t launch_scatter(int threads, int wmode, const InsertArgs &a, cudaStream_t st,
                            int query_only, KernelInfo *info);
 cudaError_t launch_merge_scratch(const InsertArgs &a, cudaStream_t st);

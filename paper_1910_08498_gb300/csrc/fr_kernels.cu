@@ -245,16 +245,7 @@ static int grid_for(size_t work, int threads, int max_blocks) {
   return (int)b;
 }
 
-static int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 1;
-  }
-  return n;
-}
+static int sm_count() { return device_sm_count(); }
 
 template <int WMODE, int KB>
 static cudaError_t launch_scatter_t(int threads, const InsertArgs &a, cudaStream_t st,
@@ -262,12 +253,9 @@ static cudaError_t launch_scatter_t(int threads, const InsertArgs &a, cudaStream
   auto fn = scatter_kernel<WMODE, KB>;
   size_t smem = WMODE == W_LUT ? (size_t)a.lut_n * sizeof(float2) : 0;
   if (info) { info->fn = (const void *)fn; info->threads = threads; info->smem = smem; }
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(WMODE == W_LUT ? 16384 * sizeof(float2) : 0));
+  if (smem) {
+    cudaError_t e = allow_dynamic_smem((const void *)fn, smem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   if (query_only) return cudaSuccess;
   if (a.n <= 0) return cudaSuccess;

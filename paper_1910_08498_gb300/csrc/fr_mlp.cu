@@ -173,16 +173,8 @@ __global__ void mlp_adam_kernel(float *P, const float *G, float *M1, float *M2, 
 static size_t smem_bytes() { return sizeof(MlpSmem); }
 
 static bool set_attrs() {
-  static bool done = false;
-  if (done) return true;
-  if (cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem_bytes()) != cudaSuccess)
-    return false;
-  if (cudaFuncSetAttribute(mlp_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem_bytes()) != cudaSuccess)
-    return false;
-  done = true;
-  return true;
+  return allow_dynamic_smem((const void *)mlp_forward_kernel, smem_bytes()) == cudaSuccess &&
+         allow_dynamic_smem((const void *)mlp_backward_kernel, smem_bytes()) == cudaSuccess;
 }
 
 size_t mlp_work_floats(int m) { return (size_t)((m + ROWS - 1) / ROWS) * (MLP_NPARAM + 1); }

@@ -712,6 +712,26 @@ int fr_config_features(int id, int S, int n, float a, float *out16) {
   return FR_OK;
 }
 
+int fr_insert_launches(fr_ctx *c, int id, int n, int *out) {
+  if (!c || !out || n < 1 || id < 0 || id >= (int)config_space().size())
+    return FR_ERR_INVALID_ARG;
+  const Config &cfg = config_space()[id];
+  if (cfg.algo == ALGO_SCATTER) {
+    *out = 2 * ((n + cfg.sub - 1) / cfg.sub);  // scatter + merge per sub-batch
+    return FR_OK;
+  }
+  InsertArgs a = base_args(c);
+  const int4 *fold = nullptr;
+  int nfold = 0, fold_split = 0;
+  int rc = gather_units(c, cfg, n, a, &fold, &nfold, &fold_split);
+  if (rc) return rc;
+  if (cfg.algo == ALGO_GATHER2)  // main launch, fold-column launch, merge if split
+    *out = 2 + ((a.any_split || fold_split) ? 1 : 0);
+  else
+    *out = 1 + (a.any_split ? 1 : 0);
+  return FR_OK;
+}
+
 int fr_count_updates(fr_ctx *c, const float *rot, int n, void *stream, unsigned long long *out) {
   if (!c || !out || n < 0 || (n > 0 && !rot)) return FR_ERR_INVALID_ARG;
   *out = 0;

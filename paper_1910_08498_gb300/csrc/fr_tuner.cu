@@ -92,9 +92,26 @@ void config_features(const Config &c, int S, int n, float a, float *f) {
   f[11] = a / 2.5f;
 }
 
-int default_config(const fr_ctx *c) {
-  // gather, 16 x 16 x 8 CTA, polynomial weights, 64-image warp lists
+int default_gather_config(const fr_ctx *c) {
+  // the per-voxel gather, 16 x 16 x 8 CTA, polynomial weights, 64-image warp lists
   const auto &sp = config_space();
+  for (int i = 0; i < (int)sp.size(); ++i)
+    if (sp[i].algo == ALGO_GATHER && sp[i].shape == 0 && sp[i].wmode == W_POLY &&
+        sp[i].chunk == 64 && config_valid(c, i))
+      return i;
+  for (int i = 0; i < (int)sp.size(); ++i)
+    if (sp[i].algo == ALGO_GATHER && config_valid(c, i)) return i;
+  return 0;
+}
+
+int default_config(const fr_ctx *c) {
+  // the direct-drain gather, 16 x 8 x 8 CTA, registers for 24 warps per SM;
+  // where it cannot run (a >= 2), the per-voxel gather default
+  const auto &sp = config_space();
+  for (int i = 0; i < (int)sp.size(); ++i)
+    if (sp[i].algo == ALGO_GATHER2 && sp[i].shape == 1 && sp[i].minw == 24 && sp[i].chunk == 64 &&
+        config_valid(c, i))
+      return i;
   for (int i = 0; i < (int)sp.size(); ++i)
     if (sp[i].algo == ALGO_GATHER && sp[i].shape == 0 && sp[i].wmode == W_POLY &&
         sp[i].chunk == 64 && config_valid(c, i))

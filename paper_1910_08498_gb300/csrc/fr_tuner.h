@@ -45,6 +45,8 @@ unsigned long long space_hash();
 // 16 normalised features of (configuration, S, n, a) for the cost model
 void config_features(const Config &c, int S, int n, float a, float *out16);
 int default_config(const fr_ctx *c);
+// the per-voxel gather's default (the persistent batched launches run that family)
+int default_gather_config(const fr_ctx *c);
 int config_valid(const fr_ctx *c, int id);
 int run_config(fr_ctx *c, int id, const void *images, int f16, const float *rot, int n,
                cudaStream_t st);

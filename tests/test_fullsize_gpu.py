@@ -41,7 +41,15 @@ def samples(batch):
     return np.array(pts), Vo, Wo
 
 
-@pytest.mark.parametrize("cfg", [13, 4, 43])
+def _first_gather2():
+    try:
+        return next(c for c in range(L.fr_num_configs())
+                    if L.fr_describe_config(c).startswith("gather2 "))
+    except Exception:
+        return 44
+
+
+@pytest.mark.parametrize("cfg", [13, 4, 43, _first_gather2(), _first_gather2() + 5])
 def test_full_size_sampled_voxels(batch, samples, cfg):
     img, rot = batch
     pts, Vo, Wo = samples
@@ -138,3 +146,45 @@ def test_full_size_whole_grid_small_batch(cfg):
     assert np.max(np.abs(Vg - Vr)) <= TOL_F32 * np.max(np.abs(Vr))
     assert np.max(np.abs(Wg - Wr)) <= TOL_F32 * np.max(np.abs(Wr))
     assert abs(Wg.sum() - Wr.sum()) <= 1e-5 * Wr.sum()
+
+
+def test_large_reconstruction_scale_sampled_voxels():
+    """The large-reconstruction scale: 20 batches of 5000 S = 256 FP32 images
+    (100,000 images, about a million terms in a voxel at the centre) into one
+    context with the tuned-space default, against the oracle on sampled
+    voxels, accumulated batch by batch; the double-float accumulators keep
+    the error at the one-batch level."""
+    S2, nb, n = 256, 20, 5000
+    H = S2 // 2
+    c = inputs.CONFIG_LARGE
+    rng = np.random.default_rng(13)
+    pts = [(0, 0, 0), (1, 0, 0), (0, 1, 1), (-1, 2, -1), (3, -2, 0)]
+    pts += [(int(rng.integers(-1, H + 1)), int(rng.integers(-H, H + 1)), int(rng.integers(-H, H + 1)))
+            for _ in range(5)]
+    Vo = np.zeros(len(pts), dtype=np.complex128)
+    Wo = np.zeros(len(pts), dtype=np.float64)
+    ctx = L.fr_create(S2, A32, ALPHA, 0, 10000)
+    try:
+        L.fr_set_options(ctx, tuning=0, forced_config=-1)
+        for b in range(nb):
+            img, rot = inputs.make_batch(S2, n, c["seed"] * 1000 + 7000 + b, device="cuda")
+            L.fr_insert(ctx, img, rot)
+            v, w = oracle.voxels(S2, img.cpu().numpy(), rot.cpu().numpy(), pts, a=A32, alpha=ALPHA)
+            Vo += v
+            Wo += w
+            del img, rot
+        D = S2 + 1
+        V = torch.empty(D ** 3, dtype=torch.complex64, device="cuda")
+        W = torch.empty(D ** 3, dtype=torch.float32, device="cuda")
+        L.fr_finalize(ctx, V, W)
+        torch.cuda.synchronize()
+        assert L.fr_last_device_error(ctx) == L.FR_OK
+        scale_v, scale_w = V.abs().max().item(), W.max().item()
+        idx = torch.tensor([((z + H) * D + (y + H)) * D + (x + H) for x, y, z in pts]).cuda()
+        Vg = V[idx].cpu().numpy().astype(np.complex128)
+        Wg = W[idx].cpu().numpy().astype(np.float64)
+    finally:
+        L.fr_destroy(ctx)
+    assert Wo[0] > 1e5  # the centre voxel sums about a million blob terms
+    assert np.max(np.abs(Vg - Vo)) <= TOL_F32 * scale_v, np.max(np.abs(Vg - Vo)) / scale_v
+    assert np.max(np.abs(Wg - Wo)) <= TOL_F32 * scale_w, np.max(np.abs(Wg - Wo)) / scale_w

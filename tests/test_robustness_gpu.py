@@ -31,7 +31,8 @@ def _finalize(ctx, S):
 
 def test_injected_launch_failure_falls_back():
     S = 32
-    batches = [inputs.make_batch(S, 80, 120 + b) for b in range(14)]
+    # enough tuning steps (4 per insert) to measure every configuration of the space
+    batches = [inputs.make_batch(S, 80, 120 + b) for b in range(20)]
     Vr, Wr, _ = oracle_insert(S, batches)
     bad = 7  # a gather configuration of the exhaustive order
     ctx = L.fr_create(S)
