@@ -27,8 +27,9 @@ Phases (one JSON line at the end):
            style): tuning overhead against the oraculum, exhaustive and
            learned search, with and without the tuning cache;
   batched  the uneven-batch workload (40 batches of S in {64..256}, n in
-           [500, 5000]): one persistent-gather graph replay per pass against
-           one fr_insert per batch;
+           [500, 5000]), FP32 and FP16 images, every batch with the
+           configuration tuned for its key: one graph replay of the
+           multi-batch launches per pass against one fr_insert per batch;
   gemm     the second dynamic-tuning workload (Sec. 5.2): batched small GEMM
            with random size changes, tuned with the paper's stop rule.
 
@@ -640,7 +641,10 @@ def run_ours(args):
     batched = None
     c3_samples = None
     if not args.no_batched:
-        batched, c3_samples = run_batched(L, inputs, dev, stream, max(2, args.steps // 3), 1, f16)
+        batched, c3_samples = {}, {}
+        for dt in ("f32", "f16"):
+            batched[dt], c3_samples[dt] = run_batched(L, inputs, dev, stream, max(2, args.steps // 3),
+                                                      1, dt == "f16")
 
     cpu = None
     precision = None
@@ -705,11 +709,52 @@ def run_ours(args):
     return 0
 
 
+def tune_batches(L, spec, data, contexts):
+    """Online tuning of the uneven-batch workload's keys: per S, one tuning
+    context inserts that S's batches with tuning on (exhaustive search) until
+    the key (S, n bucket, dtype) of every one of them is tuned; its cache is
+    saved and loaded into every context of that S, which then runs the tuned
+    best with tuning off.  Returns the chosen configuration per key, the
+    tuning inserts and their wall time."""
+    import torch
+    chosen, inserts = {}, 0
+    t0 = time.perf_counter()
+    with tempfile.TemporaryDirectory() as tmp:
+        for S in sorted({S for S, _, _ in spec}):
+            idx = [b for b, (Sb, _, _) in enumerate(spec) if Sb == S]
+            t = L.fr_create(S, 1.9, 15.0, 0, 10000)
+            L.fr_set_options(t, tuning=1)
+            pending = list(idx)
+            for _ in range(200):
+                if not pending:
+                    break
+                left = []
+                for b in pending:
+                    L.fr_insert(t, *data[b])
+                    inserts += 1
+                    rep = L.fr_tuning_report(t)
+                    if rep["tuned"]:
+                        chosen[f"S={S} n_bucket={rep['n_bucket']}"] = L.fr_describe_config(rep["best_config"])
+                    else:
+                        left.append(b)
+                pending = left
+            torch.cuda.synchronize()
+            path = os.path.join(tmp, f"tune_{S}.json")
+            L.fr_tuning_save(t, path)
+            L.fr_destroy(t)
+            for b in idx:
+                for lst in contexts:
+                    L.fr_tuning_load(lst[b], path)
+    return {"configs": chosen, "tuning_inserts": inserts,
+            "tuning_wall_s": time.perf_counter() - t0, "search": "exhaustive"}
+
+
 def run_batched(L, inputs, dev, stream, steps, warmup, f16):
     """The uneven-batch workload (40 batches, S uniform over {64, 96, 128, 192,
-    256}, n uniform over [500, 5000], one volume per batch): all batches in
-    persistent gather launches replayed from a CUDA graph, against one
-    fr_insert per batch (the same default configuration, untuned)."""
+    256}, n uniform over [500, 5000], one volume per batch), every batch with
+    the configuration the tuner picked for its key (tune_batches, untimed): all
+    batches in multi-batch launches replayed from a CUDA graph, against one
+    fr_insert per batch with the same configurations."""
     import torch
     spec = inputs.uneven_batches()
     data, ctx_p, ctx_s = [], [], []
@@ -726,6 +771,7 @@ def run_batched(L, inputs, dev, stream, steps, warmup, f16):
             L.fr_set_options(c, tuning=0, forced_config=-1)
             lst.append(c)
         ups += L.fr_count_updates(ctx_p[-1], rot)
+    tuning = tune_batches(L, spec, data, (ctx_p, ctx_s))
     imgs = [d[0] for d in data]
     rots = [d[1] for d in data]
 
@@ -749,6 +795,7 @@ def run_batched(L, inputs, dev, stream, steps, warmup, f16):
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3 / steps
         out[name] = {"value": ups / t, "ms_per_pass": 1e3 * t}
+    out["speedup"] = out["persistent_graph"]["value"] / out["per_batch_inserts"]["value"]
     # one persistent pass into cleared volumes, sampled per batch (compared
     # with the FP64 oracle in the cpu_baseline leg)
     for c in ctx_p:
@@ -762,7 +809,8 @@ def run_batched(L, inputs, dev, stream, steps, warmup, f16):
     sizes = sorted({S for S, _, _ in spec})
     return ({"workload": f"{len(spec)} batches, S in {sizes}, n in [500, 5000] (seeded), one volume each, "
                          f"{'FP16' if f16 else 'FP32'} images",
-             "updates_per_pass": ups, "images_per_pass": sum(n for _, n, _ in spec), **out},
+             "updates_per_pass": ups, "images_per_pass": sum(n for _, n, _ in spec),
+             "tuning": tuning, **out},
             {"f16": f16, "batches": samples})
 
 
@@ -792,22 +840,25 @@ def run_precision(prec_gpu, batch0, S, a, f16_run, c3, dev, inputs):
                                    pts, a=a, alpha=15.0)
             out["f16"] = {"vs_f32_values": sample_errors(prec_gpu["f16"], Vo, Wo),
                           "vs_f16_values": sample_errors(prec_gpu["f16"], Vh, Wh)}
-    if c3:
+    for key, c3s in (c3 or {}).items():
         per = []
-        for (Sb, n, seed), g in c3["batches"]:
+        for (Sb, n, seed), g in c3s["batches"]:
             gen = torch.Generator(device=dev)
             gen.manual_seed(seed)
             rb = inputs.random_rotations(n, gen, dev)
             ib = inputs.random_images(Sb, n, gen, dev)
-            if c3["f16"]:
+            if c3s["f16"]:
                 ib = inputs.half_values(inputs.to_half(ib))
             Vb, Wb = oracle.voxels(Sb, ib.cpu().numpy(), rb.cpu().numpy(), g["pts"], a=a, alpha=15.0)
             e = sample_errors(g, Vb, Wb)
             per.append({"S": Sb, "n": n, "err_V": e["err_V"], "err_W": e["err_W"]})
             del ib, rb
-        out["c3"] = {"images": "FP16 (vs the FP16-rounded values)" if c3["f16"] else "FP32",
-                     "batches": len(per), "max_err_V": max(p["err_V"] for p in per),
-                     "max_err_W": max(p["err_W"] for p in per), "per_batch": per}
+        out.setdefault("c3", {})[key] = {
+            "images": "FP16 (vs the FP16-rounded values)" if c3s["f16"] else "FP32",
+            "batches": len(per), "max_err_V": max(p["err_V"] for p in per),
+            "max_err_W": max(p["err_W"] for p in per), "per_batch": per}
+        out.setdefault("c3_max", {})[key] = {"err_V": max(p["err_V"] for p in per),
+                                             "err_W": max(p["err_W"] for p in per)}
     return out
 
 

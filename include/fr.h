@@ -157,28 +157,40 @@ int fr_reset(fr_ctx *ctx, void *stream);
  * device, [n][9] float32.  0 <= n <= 2^24; n = 0 is a no-op.  Every image is
  * inserted exactly once whatever the tuning state: while tuning, the batch may
  * be split into sub-batches, each run with a different configuration and
- * timed with CUDA events (non-blocking dynamic tuning, Sec. 3.2).  The S of
- * the images is the context's S; a new batch-size bucket starts a new tuning
- * key (cached keys are reused). */
+ * timed with CUDA events (non-blocking dynamic tuning, Sec. 3.2).  When the
+ * search ran in such sub-batch steps, the fastest configuration of each kernel
+ * family (direct-drain gather, per-voxel gather, scatter) then runs one whole
+ * insert each, and the key's best is the fastest of those whole-insert
+ * timings (a gather launch has a fixed cost that a small step does not
+ * amortise).  The S of the images is the context's S; a new batch-size bucket
+ * starts a new tuning key (cached keys are reused).  images must be 16-byte
+ * aligned. */
 int fr_insert(fr_ctx *ctx, const void *images, fr_dtype dtype, const float *rotations,
               int n, void *stream);
 
 /* Insert nb batches, batch b into context ctxs[b] (contexts may differ in S
- * and blob and may repeat).  All arrays are host arrays of nb entries;
- * images[b] and rotations[b] are device pointers.  Each batch runs the gather
- * configuration its context's tuner picked for its key (or the default; a
- * scatter choice is replaced by the default gather).  Batches that share
- * brick shape, candidate-box width, image dtype and list capacity run in ONE
- * persistent kernel launch: each CTA takes work units (a brick and a share of
- * a batch's images) from a device counter, heaviest units first, so uneven S
- * and n share the GPU without a tail per batch.  A context that appears more than once receives
- * its sums through its scratch volume with atomics.  The first call with a
- * given (contexts, pointers, sizes, dtypes, configurations) builds a plan and
- * uploads it (synchronously); later calls reuse it.  With capture = 1 the
- * plan's launch sequence (counter reset, persistent kernels, scratch merges)
- * is captured, on a stream the library owns, into a CUDA graph at the first
- * call; that call and later ones launch the graph on `stream`.  Same semantics per batch as fr_insert (every image exactly once);
- * no tuning steps are taken here. */
+ * and blob and may repeat): several samples in one launch, which the atomic
+ * accumulation makes possible (Sec. 5.3.2).  All arrays are host arrays of nb
+ * entries; images[b] (16-byte aligned) and rotations[b] are device pointers.
+ * Each batch runs the configuration its context's tuner picked for its key
+ * (else the context's forced configuration or the default).  Batches whose
+ * configurations share a kernel instantiation run in ONE launch over the
+ * pooled work units (a brick and a share of a batch's images) of all of them,
+ * heaviest units first, so uneven S and n share the GPU without a tail per
+ * batch: the direct-drain gather as one CTA per unit (its fold columns in a
+ * second launch on a high-priority side stream), the per-voxel gather as a
+ * persistent kernel whose CTAs take units from a device counter.  Batches
+ * whose configuration has no multi-batch kernel (scatter, tabulated weights)
+ * run their own launches after those.  A context that appears more than once
+ * receives its sums through its scratch volume with atomics.  The first call
+ * with a given (contexts, pointers, sizes, dtypes, configurations) builds a
+ * plan and uploads it (synchronously); later calls reuse it.  With capture =
+ * 1 the plan's launch sequence is captured, on a stream the library owns,
+ * into a CUDA graph at the first call; that call and later ones launch the
+ * graph on `stream`.  Same semantics per batch as fr_insert (every image
+ * exactly once); no tuning steps are taken here.  Returns FR_ERR_INVALID_ARG
+ * for a null context, a misaligned or null pointer with n > 0, n out of
+ * range, a bad dtype or contexts on different devices. */
 int fr_insert_batched(fr_ctx *const *ctxs, const void *const *images, const fr_dtype *dtypes,
                       const float *const *rotations, const int *n, int nb, int capture,
                       void *stream);

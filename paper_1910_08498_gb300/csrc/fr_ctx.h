@@ -35,14 +35,14 @@ struct fr_ctx {
   struct Units {
     int shape = -1, n = -1, count = 0, any_split = 0, algo = 0;
     int4 *dev = nullptr;
-    // row-class gather: the per-voxel gather's units over the fold columns
+    // direct-drain gather: the per-voxel gather's units over the fold columns
     // (x <= floor(a)), stored after the main units in dev
     int fold_count = 0, fold_split = 0;
     const int4 *fold = nullptr;
   };
   Units units[8];
   unsigned long long *d_phase = nullptr;  // gather phase counters (debug bit 1)
-  // side stream (highest priority) and fork/join events: the row-class
+  // side stream (highest priority) and fork/join events: the direct-drain
   // gather's fold-column launch runs beside its main launch
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -76,7 +76,10 @@ double gather_unit_loads(const fr_ctx *c, int shape, int n, double target,
                          std::vector<UnitLoad> &out, int &any_split);
 // work units of bricks of shape sh tiling x in [x0, x1] (all y, z), split so
 // that no unit exceeds `target` expected images (target <= 0: the total over
-// per_sm units per SM); returns the total expected load
+// per_sm units per SM, at least UNIT_MIN_LOAD), into at most 64 units of at
+// least SPLIT_MIN_IMAGES images per brick; returns the total expected load
+constexpr double UNIT_MIN_LOAD = 16.0;
+constexpr int SPLIT_MIN_IMAGES = 8;
 double brick_unit_loads(const fr_ctx *c, const GatherShape &sh, int x0, int x1, int n,
                         double target, int per_sm, std::vector<UnitLoad> &out, int &any_split);
 // drop cached batched-insertion plans that refer to c (called by fr_destroy)

@@ -547,7 +547,8 @@ constexpr size_t GATHER_ARGS_BYTES = (sizeof(InsertArgs) + 15) & ~(size_t)15;
 // wsmem is the warp's gather_warp_smem(args.chunk) bytes; lut the shared blob
 // table (W_LUT only).  No CTA-wide barrier is taken.
 template <int BX, int BY, int ZC, int WMODE, int KB, int F16>
-__device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2 *lut,
+__device__ __forceinline__ void gather_warp(const InsertArgs &args, const InsertArgs &cst,
+                                            const void *images, const float2 *lut,
                                             unsigned char *wsmem, const int4 unit,
                                             const int warp) {
   constexpr int WV = 32 * ZC;                   // voxels per warp footprint
@@ -556,9 +557,9 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
   static_assert(BX % 8 == 0 && BY % 4 == 0 && (BX * BY) % 32 == 0,
                 "warp footprint is 8 x 4 columns");
   static_assert(ZC <= 8, "item encoding holds 3 bits of z");
-  const Geom &g = args.g;
+  const Geom &g = cst.g;
   const int lane = threadIdx.x & 31;
-  const int lcap = args.chunk;  // list capacity per warp (<= 128: 7 bits of the item tags)
+  const int lcap = cst.chunk;  // list capacity per warp (<= 128: 7 bits of the item tags)
   if (lcap > 128) {
     if ((threadIdx.x & 31) == 0) set_err(args.err, DERR_RANGE);
     return;
@@ -585,8 +586,8 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
   const int fx0 = g.xa0 + unit.x * BX + wx * 8;
   const int fy0 = -g.H + unit.y * BY + wy * 4;
   const int z0 = -g.H + unit.z * ZC;
-  // the row-class gather leaves the fold columns (x <= floor(a)) to this one
-  if (args.fold_only && fx0 > -g.xa0) return;
+  // the direct-drain gather leaves the fold columns (x <= floor(a)) to this one
+  if (cst.fold_only && fx0 > -g.xa0) return;
   const float cx = fx0 + 3.5f, cy = fy0 + 1.5f, cz = z0 + 0.5f * (ZC - 1);  // footprint centre
   const float hz = 0.5f * (ZC - 1);
   const float rw = sqrtf(3.5f * 3.5f + 1.5f * 1.5f + hz * hz);
@@ -603,13 +604,13 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
   const int vx = fx0 + (lane & 7), vy = fy0 + (lane >> 3);
   const float dvx = (float)vx - cx, dvy = (float)vy - cy;
   const bool fold_col = vx <= -g.xa0;  // x <= floor(a): pixels from both sides of the fold
-  // with fold_only, the columns x > floor(a) belong to the row-class gather
-  const bool col_in = vx <= g.H && vy <= g.H && (!args.fold_only || fold_col);
-  const unsigned char *imgs = reinterpret_cast<const unsigned char *>(args.images);
+  // with fold_only, the columns x > floor(a) belong to the direct-drain gather
+  const bool col_in = vx <= g.H && vy <= g.H && (!cst.fold_only || fold_col);
+  const unsigned char *imgs = reinterpret_cast<const unsigned char *>(images);
   const size_t img_stride = (size_t)g.S * g.NX * ESZ;
   float2 cpair[POLY_N / 2];
 #pragma unroll
-  for (int k = 0; k < POLY_N / 2; ++k) cpair[k] = make_float2(args.poly[2 * k], args.poly[2 * k + 1]);
+  for (int k = 0; k < POLY_N / 2; ++k) cpair[k] = make_float2(cst.poly[2 * k], cst.poly[2 * k + 1]);
 
   for (int i = lane; i < 3 * WV; i += 32) s_acc[i] = 0.f;
   __syncwarp();
@@ -650,27 +651,27 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const float2
     if (kind == 0 || (kind == 1 && WMODE == W_POLY)) {
       if (WMODE == W_POLY) {
         if (kind == 0)
-          box_poly_interior<KB, F16>(args, cpair, ibase, sgn, kx0, ky0, fx, fy, uz2,
+          box_poly_interior<KB, F16>(cst, cpair, ibase, sgn, kx0, ky0, fx, fy, uz2,
                                      2.0f * inv_a2, sr, si, sw);
         else
-          box_poly_edge<KB, F16>(args, cpair, ibase, sgn, kx0, ky0, fx, fy, uz2, 2.0f * inv_a2,
+          box_poly_edge<KB, F16>(cst, cpair, ibase, sgn, kx0, ky0, fx, fy, uz2, 2.0f * inv_a2,
                                  sr, si, sw);
       } else {
-        box_fast<WMODE, KB, F16>(args, lut, ibase, sgn, kx0, ky0, fx, fy, uz2, inv_a2, sr, si, sw);
+        box_fast<WMODE, KB, F16>(cst, lut, ibase, sgn, kx0, ky0, fx, fy, uz2, inv_a2, sr, si, sw);
       }
       si *= (float)sgn;
     } else if (kind == 2 && WMODE == W_POLY) {
       // a box crossing kx = 0 for a voxel away from the fold plane
-      box_poly_straddle<KB, F16>(args, cpair, ibase, kx0, ky0, fx, fy, uz2, 2.0f * inv_a2, sr,
+      box_poly_straddle<KB, F16>(cst, cpair, ibase, kx0, ky0, fx, fy, uz2, 2.0f * inv_a2, sr,
                                  si, sw);
     } else {
       const float e[6] = {LF(LF_E1X, li), LF(LF_E1Y, li), LF(LF_E1Z, li),
                           LF(LF_E2X, li), LF(LF_E2Y, li), LF(LF_E2Z, li)};
       if (kind == 3 && WMODE == W_POLY)
-        box_poly_fold<KB, F16>(args, cpair, ibase, e, kx0, ky0, fx, fy, uz2, sx, sy, sz,
+        box_poly_fold<KB, F16>(cst, cpair, ibase, e, kx0, ky0, fx, fy, uz2, sx, sy, sz,
                                2.0f * inv_a2, sr, si, sw);
       else
-        box_careful<WMODE, KB, F16>(args, lut, ibase, e, kx0, ky0, fx, fy, uz2, kind == 3, sx,
+        box_careful<WMODE, KB, F16>(cst, lut, ibase, e, kx0, ky0, fx, fy, uz2, kind == 3, sx,
                                     sy, sz, inv_a2, sr, si, sw);
     }
     const int slot = src * ZC + t;
@@ -903,7 +904,8 @@ gather_kernel(const InsertArgs args) {
     for (int i = tid; i < args.lut_n; i += NT) s_lut[i] = args.lut[i];
     __syncthreads();  // the only CTA-wide barrier: warps run independently from here
   }
-  gather_warp<BX, BY, ZC, WMODE, KB, F16>(args, s_lut, sp + (size_t)warp * gather_warp_smem(ZC, args.chunk),
+  gather_warp<BX, BY, ZC, WMODE, KB, F16>(args, args, args.images, s_lut,
+                                          sp + (size_t)warp * gather_warp_smem(ZC, args.chunk),
                                           args.units[blockIdx.x], warp);
 }
 
@@ -943,9 +945,34 @@ gather_persistent_kernel(const InsertArgs *__restrict__ descs, const int4 *__res
     }
     __syncthreads();
     const int4 unit = make_int4(it.x & 1023, (it.x >> 10) & 1023, (it.x >> 20) & 1023, it.y);
-    gather_warp<BX, BY, ZC, WMODE, KB, F16>(*s_args, nullptr, wsmem, unit, warp);
+    gather_warp<BX, BY, ZC, WMODE, KB, F16>(*s_args, *s_args, s_args->images, nullptr, wsmem,
+                                            unit, warp);
     __syncthreads();  // s_item and s_args are rewritten next
   }
+}
+
+// Several batches in one launch, one CTA per work item: CTA b takes
+// p.items[b] (encoded as for the persistent gather) and copies its batch's
+// arguments p.descs[batch] to shared memory; geometry, weights and list
+// capacity, common to the launch's batches, are read from p.base (kernel
+// parameters).  Weights on the fly.
+template <int BX, int BY, int ZC, int WMODE, int KB, int F16>
+__global__ void __launch_bounds__(BX * BY, 512 / (BX * BY))
+gather_multi_kernel(const MultiLaunch p) {
+  static_assert(WMODE != W_LUT, "the multi-batch gather evaluates weights on the fly");
+  constexpr int NT = BX * BY;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  extern __shared__ __align__(16) unsigned char smem[];
+  InsertArgs *s_args = reinterpret_cast<InsertArgs *>(smem);
+  const int4 it = p.items[blockIdx.x];
+  const int *src = reinterpret_cast<const int *>(p.descs + it.z);
+  int *dst = reinterpret_cast<int *>(s_args);
+  for (int i = tid; i < (int)(sizeof(InsertArgs) / 4); i += NT) dst[i] = src[i];
+  __syncthreads();
+  const int4 unit = make_int4(it.x & 1023, (it.x >> 10) & 1023, (it.x >> 20) & 1023, it.y);
+  gather_warp<BX, BY, ZC, WMODE, KB, F16>(
+      *s_args, p.base, p.images[it.w], nullptr,
+      smem + GATHER_ARGS_BYTES + (size_t)warp * gather_warp_smem(ZC, p.base.chunk), unit, warp);
 }
 
 }  // namespace fr

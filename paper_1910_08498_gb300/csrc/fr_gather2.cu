@@ -71,6 +71,22 @@ int resident_ctas(const void *fn, int threads, size_t smem) {
   return per_sm;
 }
 
+cudaError_t launch_multi(const void *fn, const MultiLaunch &p, int threads, size_t smem,
+                         cudaStream_t st) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)p.nitems);
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = p.priority;
+  cfg.attrs = attr;
+  cfg.numAttrs = p.priority != 0 ? 1 : 0;
+  void *params[] = {const_cast<MultiLaunch *>(&p)};
+  return cudaLaunchKernelExC(&cfg, fn, params);
+}
+
 size_t gather2_smem_bytes(const GatherShape &sh, int chunk) {
   const int nw = sh.bx * sh.by / 32;
   return (size_t)nw * (sh.zc == 8 ? gather2_warp_smem<8>(chunk) : gather2_warp_smem<16>(chunk));
@@ -91,6 +107,21 @@ cudaError_t launch_gather2_shape1(int minw, const InsertArgs &a, cudaStream_t st
                                   KernelInfo *info);
 cudaError_t launch_gather2_shape2(int minw, const InsertArgs &a, cudaStream_t st, int query_only,
                                   KernelInfo *info);
+
+cudaError_t launch_gather2_multi_shape0(int minw, int f16, const MultiLaunch &p, cudaStream_t st);
+cudaError_t launch_gather2_multi_shape1(int minw, int f16, const MultiLaunch &p, cudaStream_t st);
+cudaError_t launch_gather2_multi_shape2(int minw, int f16, const MultiLaunch &p, cudaStream_t st);
+
+cudaError_t launch_gather2_multi(int shape_id, int minw, int f16, const MultiLaunch &p,
+                                 cudaStream_t st) {
+  if (p.base.chunk > 64 || p.base.g.KB != 4) return cudaErrorInvalidValue;
+  switch (shape_id) {
+    case 0: return launch_gather2_multi_shape0(minw, f16, p, st);
+    case 1: return launch_gather2_multi_shape1(minw, f16, p, st);
+    case 2: return launch_gather2_multi_shape2(minw, f16, p, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_gather2(int shape_id, int minw, const InsertArgs &a, cudaStream_t st,
                            int query_only, KernelInfo *info) {

@@ -95,13 +95,13 @@ __device__ __forceinline__ void load_row4(const unsigned char *row, float2 &p0, 
 // u_z^2 = uz2; returns the sums of w p (complex) and of w over the candidates
 // with r <= a.
 template <int F16>
-__device__ __forceinline__ void g2_box(const InsertArgs &args, const unsigned char *ibase, int ky0,
-                                       float fx, float fy, float uz2, float cs, float sq,
-                                       float2 &acc, float &aw) {
+__device__ __forceinline__ void g2_box(const InsertArgs &args, const float2 *cp,
+                                       const unsigned char *ibase, int ky0, float fx, float fy,
+                                       float uz2, float cs, float sq, float2 &acc, float &aw) {
   constexpr int NP = POLY_N;
   constexpr int ESZ = F16 ? 4 : 8;
   const Geom &g = args.g;
-  const float2 *cp = args.poly2;  // coefficient pairs (c_k, c_k), kernel-parameter constants
+  // cp: coefficient pairs (c_k, c_k), kernel-parameter constants
   const int row_bytes = g.NX * ESZ;
   // scaled column offsets sq (fx - j): x = (sq dx)^2 + cs (dy^2 + u_z^2) - 1
   const float2 d01 = make_float2(sq * fx, sq * (fx - 1.0f));
@@ -137,14 +137,18 @@ __device__ __forceinline__ void g2_box(const InsertArgs &args, const unsigned ch
 }
 
 // One warp's share of one work unit (see gather_warp for the unit word).
+// args: the batch's arguments; cst: the arguments its launch shares (geometry,
+// weight polynomial, list capacity) and images the batch's images, both read
+// in the inner loops.
 template <int BX, int BY, int ZC, int F16>
-__device__ __forceinline__ void gather2_warp(const InsertArgs &args, unsigned char *wsmem,
+__device__ __forceinline__ void gather2_warp(const InsertArgs &args, const InsertArgs &cst,
+                                             const void *images, unsigned char *wsmem,
                                              const int4 unit, const int warp) {
   static_assert(BX % 8 == 0 && BY % 4 == 0 && (BX * BY) % 32 == 0, "warp footprint is 8 x 4");
   static_assert(ZC == 8 || ZC == 16, "tags hold 4 bits of z");
   constexpr int WV = 32 * ZC;
   constexpr int ESZ = F16 ? 4 : 8;
-  const Geom &g = args.g;
+  const Geom &g = cst.g;
   const int lane = threadIdx.x & 31;
   const int wx = warp % (BX / 8), wy = warp / (BX / 8);
   // the bricks tile x >= floor(a) + 1: the fold columns x <= floor(a) are
@@ -152,7 +156,7 @@ __device__ __forceinline__ void gather2_warp(const InsertArgs &args, unsigned ch
   const int fx0 = 1 - g.xa0 + unit.x * BX + wx * 8;
   const int fy0 = -g.H + unit.y * BY + wy * 4;
   const int z0 = -g.H + unit.z * ZC;
-  const int lcap = args.chunk;
+  const int lcap = cst.chunk;
   if (lcap > 64) {  // list entries are 6 bits of the tags
     if (lane == 0) set_err(args.err, DERR_RANGE);
     return;
@@ -182,7 +186,7 @@ __device__ __forceinline__ void gather2_warp(const InsertArgs &args, unsigned ch
   const bool col_in = vx <= g.H && vy <= g.H;
   const float dvx = (float)(lane & 7) - 3.5f, dvy = (float)(lane >> 3) - 1.5f;
   const float cs = 2.0f / g.a2, sq = sqrtf(cs);  // the weight polynomial's argument scales
-  const unsigned char *imgs = reinterpret_cast<const unsigned char *>(args.images);
+  const unsigned char *imgs = reinterpret_cast<const unsigned char *>(images);
   const size_t img_stride = (size_t)g.S * g.NX * ESZ;
   const unsigned lt = (1u << lane) - 1u;
 
@@ -240,8 +244,8 @@ __device__ __forceinline__ void gather2_warp(const InsertArgs &args, unsigned ch
     const float fy = vyr - iyf + (float)(ky0 - kyc);
     float2 acc;
     float aw;
-    g2_box<F16>(args, imgs + (size_t)q3.z * img_stride + (size_t)kxc * ESZ, kyc, fx, fy, uz * uz,
-                cs, sq, acc, aw);
+    g2_box<F16>(cst, cst.poly2, imgs + (size_t)q3.z * img_stride + (size_t)kxc * ESZ, kyc, fx, fy,
+                uz * uz, cs, sq, acc, aw);
     if (valid) {
       const int slot = src * ZC + t;
       atomicAdd(&s_acc[slot], acc.x);
@@ -379,8 +383,32 @@ __global__ void __launch_bounds__(BX * BY, MINW * 32 / (BX * BY))
 gather2_kernel(const InsertArgs args) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5;
-  gather2_warp<BX, BY, ZC, F16>(args, smem + (size_t)warp * gather2_warp_smem<ZC>(args.chunk),
+  gather2_warp<BX, BY, ZC, F16>(args, args, args.images,
+                                smem + (size_t)warp * gather2_warp_smem<ZC>(args.chunk),
                                 args.units[blockIdx.x], warp);
+}
+
+// Several batches in one launch: CTA b takes work item p.items[b] =
+// {bx | by << 10 | bz << 20, split word, batch, slot} and copies its batch's
+// arguments p.descs[batch] to shared memory; geometry, weight polynomial and
+// list capacity, common to the launch's batches, are read from p.base (kernel
+// parameters: constant operands in the inner loops).
+template <int BX, int BY, int ZC, int F16, int MINW>
+__global__ void __launch_bounds__(BX * BY, MINW * 32 / (BX * BY))
+gather2_multi_kernel(const MultiLaunch p) {
+  constexpr int NT = BX * BY;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  InsertArgs *s_args = reinterpret_cast<InsertArgs *>(smem);
+  const int4 it = p.items[blockIdx.x];
+  const int *src = reinterpret_cast<const int *>(p.descs + it.z);
+  int *dst = reinterpret_cast<int *>(s_args);
+  for (int i = tid; i < (int)(sizeof(InsertArgs) / 4); i += NT) dst[i] = src[i];
+  __syncthreads();
+  const int4 unit = make_int4(it.x & 1023, (it.x >> 10) & 1023, (it.x >> 20) & 1023, it.y);
+  gather2_warp<BX, BY, ZC, F16>(
+      *s_args, p.base, p.images[it.w],
+      smem + GATHER_ARGS_BYTES + (size_t)warp * gather2_warp_smem<ZC>(p.base.chunk), unit, warp);
 }
 
 }  // namespace fr

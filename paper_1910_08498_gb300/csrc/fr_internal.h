@@ -145,6 +145,28 @@ struct PersistentLaunch {
 cudaError_t launch_gather_persistent(int shape_id, int kb, int f16, const PersistentLaunch &p,
                                      cudaStream_t st);
 
+// One launch over the work items of several batches, one CTA per item (the
+// hardware block scheduler hands out the items, heaviest first).  The
+// batches of one launch share S, blob, dtype and configuration: what they
+// share stays in the kernel parameters (base), the rest is read per batch.
+constexpr int MULTI_MAX = 64;  // batches per multi-batch launch
+struct MultiLaunch {
+  InsertArgs base;           // common arguments: geometry, weights, list capacity, fold_only
+  const InsertArgs *descs;   // device, one per batch (images, rot, n, acc, scratch, err)
+  const int4 *items;         // device, {bx | by << 10 | bz << 20, split word, batch, slot}
+  int nitems;
+  int priority;              // launch priority (cudaLaunchAttributePriority), 0 = the stream's
+  const void *images[MULTI_MAX];  // images of the launch's batches, by slot (read in the inner loop)
+};
+// launch kernel fn (taking one MultiLaunch) with p.nitems CTAs, at p.priority
+cudaError_t launch_multi(const void *fn, const MultiLaunch &p, int threads, size_t smem,
+                         cudaStream_t st);
+// the direct-drain gather (fold columns excluded), FP32 or FP16 images
+cudaError_t launch_gather2_multi(int shape_id, int minw, int f16, const MultiLaunch &p,
+                                 cudaStream_t st);
+// the per-voxel gather over the fold columns (descs with fold_only set)
+cudaError_t launch_gather_fold_multi(int f16, const MultiLaunch &p, cudaStream_t st);
+
 // MLP kernels
 cudaError_t mlp_forward(const float *params, const float *x, int m, float *y, cudaStream_t st);
 cudaError_t mlp_backward(const float *params, const float *x, const float *t, int m, float *grad,

@@ -138,7 +138,11 @@ int ensure_scratch(fr_ctx *c) {
 // n min(1, (a + r) / d).  Bricks whose count exceeds a target share are split
 // into several units, each taking a contiguous range of the images.  `target`
 // <= 0 selects the share of one launch of this batch alone (total load over
-// 32 units per SM).  Returns the units with their expected loads, unsorted.
+// per_sm units per SM, at least UNIT_MIN_LOAD).  Every plane crosses the
+// bricks at the centre, whose warps take the images of their unit one after
+// another: the split floor bounds that serial path (at most 64 units per
+// brick, at least SPLIT_MIN_IMAGES images each).  Returns the units with
+// their expected loads, unsorted.
 double brick_unit_loads(const fr_ctx *c, const GatherShape &sh, int x0, int x1, int n,
                         double target, int per_sm, std::vector<UnitLoad> &out, int &any_split) {
   const Geom &g = c->g;
@@ -164,7 +168,7 @@ double brick_unit_loads(const fr_ctx *c, const GatherShape &sh, int x0, int x1, 
   if (target <= 0) {
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    target = std::max(64.0, total / (std::max(sms, 1) * (double)per_sm));
+    target = std::max(UNIT_MIN_LOAD, total / (std::max(sms, 1) * (double)per_sm));
   }
   out.clear();
   out.reserve(load.size() + 64);
@@ -174,7 +178,7 @@ double brick_unit_loads(const fr_ctx *c, const GatherShape &sh, int x0, int x1, 
       for (int bx = 0; bx < nbx; ++bx) {
         const double l = load[((size_t)bz * nby + by) * nbx + bx];
         int ns = (int)std::ceil(l / target);
-        ns = std::max(1, std::min(ns, std::min(64, std::max(1, n / 32))));
+        ns = std::max(1, std::min(ns, std::min(64, std::max(1, n / SPLIT_MIN_IMAGES))));
         if (ns > 1) any_split = 1;
         for (int s = 0; s < ns; ++s)
           out.push_back(UnitLoad{l / ns, make_int4(bx, by, bz, s | (ns << 16))});
@@ -207,7 +211,7 @@ static int gather_units(fr_ctx *c, const Config &cfg, int n, InsertArgs &a,
   std::vector<UnitLoad> us, fs;
   int any_split = 0, fsplit = 0;
   if (algo == ALGO_GATHER2) {
-    // the row-class gather's bricks tile x in [floor(a) + 1, H]; the fold
+    // the direct-drain gather's bricks tile x in [floor(a) + 1, H]; the fold
     // columns x in [-floor(a), floor(a)] go to the per-voxel gather in
     // bricks one footprint wide, split finely (they are few and heavy)
     brick_unit_loads(c, gather2_shape(cfg.shape), 1 - c->g.xa0, c->g.H, n, 0.0, 32, us, any_split);
@@ -425,7 +429,7 @@ int fr::do_insert_ctx(fr_ctx *c, const void *images, fr_dtype dtype, const float
       c->tuner.end(tm, ks, fb, s.images, false, st);
       status = FR_ERR_LAUNCH;
     } else {
-      c->tuner.end(tm, ks, s.config, s.images, s.tuning, st);
+      c->tuner.end(tm, ks, s.config, s.images, s.tuning, st, s.full);
     }
     if (nvtx) nvtxRangePop();
     ks.last_config = s.config;

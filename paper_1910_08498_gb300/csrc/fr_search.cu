@@ -32,7 +32,7 @@ std::vector<std::vector<int>> config_neighbours(const std::vector<int> &valid) {
           diff = (a.threads != b.threads) + (a.wmode != b.wmode) + (a.sub != b.sub);
         adj = diff == 1;
       } else if (a.algo == ALGO_GATHER2 || b.algo == ALGO_GATHER2) {
-        // the row-class gather neighbours the per-voxel gather of its brick
+        // the direct-drain gather neighbours the per-voxel gather of its brick
         // shape and list capacity with polynomial weights (and nothing else)
         const Config &g2 = a.algo == ALGO_GATHER2 ? a : b, &o = a.algo == ALGO_GATHER2 ? b : a;
         adj = o.algo == ALGO_GATHER && o.shape == g2.shape && o.chunk == g2.chunk &&

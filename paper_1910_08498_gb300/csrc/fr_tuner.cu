@@ -234,6 +234,15 @@ std::vector<Step> Tuner::plan(KeyState &ks, int n, const fr_options &opt) {
     steps.push_back(Step{fallback, n, false});
     return steps;
   }
+  if (ks.confirming) {
+    // the finalists, one whole insert each; then the best so far until
+    // their timings are harvested
+    if (ks.fin_next < ks.finalists.size())
+      steps.push_back(Step{ks.finalists[ks.fin_next++], n, true, true});
+    else
+      steps.push_back(Step{fallback, n, false});
+    return steps;
+  }
   if (ks.adaptive) {
     // decide the proposals whose times are known, then propose this insert's steps
     ks.walker.decide([&](int c) -> double {
@@ -255,6 +264,7 @@ std::vector<Step> Tuner::plan(KeyState &ks, int n, const fr_options &opt) {
     }
     ks.proposed += (int)cfgs.size();
     const int m = (int)cfgs.size();
+    if (m > 1) ks.sub_steps = true;
     const int base = n / m, extra = n % m;
     for (int i = 0; i < m; ++i) steps.push_back(Step{cfgs[i], base + (i < extra ? 1 : 0), true});
     return steps;
@@ -267,6 +277,7 @@ std::vector<Step> Tuner::plan(KeyState &ks, int n, const fr_options &opt) {
     return steps;
   }
   int k = std::min(std::min(kmax, remaining), n);
+  if (k > 1) ks.sub_steps = true;
   int base = n / k, extra = n % k;
   for (int i = 0; i < k; ++i) {
     int cfg = ks.order[ks.next++];
@@ -283,10 +294,14 @@ Timing Tuner::begin(cudaStream_t st) {
   return t;
 }
 
-void Tuner::end(Timing t, KeyState &ks, int config, int images, bool tuning, cudaStream_t st) {
+void Tuner::end(Timing t, KeyState &ks, int config, int images, bool tuning, cudaStream_t st,
+                bool full) {
   cudaEventRecord(t.stop, st);
-  pending_.push_back(Pending{t, &ks, config, images, tuning});
-  if (tuning) ++ks.pending;
+  pending_.push_back(Pending{t, &ks, config, images, tuning, full});
+  if (full)
+    ++ks.fin_pending;
+  else if (tuning)
+    ++ks.pending;
 }
 
 void Tuner::abandon(Timing t) {
@@ -294,23 +309,54 @@ void Tuner::abandon(Timing t) {
   pool_.push_back(t.stop);
 }
 
-void Tuner::update_best(KeyState &ks) {
+static int fastest(const std::map<int, Meas> &meas, const std::set<int> &invalid, int algo) {
   int best = -1;
   double bt = 0;
-  for (auto &m : ks.meas) {
-    if (m.second.images <= 0 || ks.invalid.count(m.first)) continue;
+  for (auto &m : meas) {
+    if (m.second.images <= 0 || invalid.count(m.first)) continue;
+    if (algo >= 0 && config_space()[m.first].algo != algo) continue;
     double t = m.second.per_image();
     if (best < 0 || t < bt) { best = m.first; bt = t; }
   }
+  return best;
+}
+
+// the best so far: the fastest screened configuration, or the fastest
+// finalist once confirmed; final once the key is tuned
+void Tuner::update_best(KeyState &ks) {
+  if (ks.tuned) return;
+  int best = ks.confirmed ? fastest(ks.full, ks.invalid, -1) : -1;
+  if (best < 0) best = fastest(ks.meas, ks.invalid, -1);
   ks.best = best;
 }
 
 void Tuner::finish_if_done(KeyState &ks) {
+  if (ks.tuned) return;
   const bool exhausted = ks.adaptive ? ks.proposed >= ks.budget : ks.next >= ks.order.size();
-  if (!ks.tuned && exhausted && ks.pending == 0) {
+  if (!exhausted || ks.pending != 0) return;
+  if (!ks.confirming) {
     update_best(ks);
+    ks.finalists.clear();
+    if (ks.sub_steps) {
+      std::vector<std::pair<double, int>> fam;
+      for (int algo : {ALGO_GATHER2, ALGO_GATHER, ALGO_SCATTER}) {
+        const int f = fastest(ks.meas, ks.invalid, algo);
+        if (f >= 0) fam.push_back({ks.meas[f].per_image(), f});
+      }
+      std::sort(fam.begin(), fam.end());
+      for (auto &x : fam) ks.finalists.push_back(x.second);
+    }
+    if (ks.finalists.size() > 1) {
+      ks.confirming = true;
+      return;
+    }
     ks.tuned = ks.best >= 0;
+    return;
   }
+  if (ks.fin_next < ks.finalists.size() || ks.fin_pending > 0) return;
+  ks.confirmed = true;
+  update_best(ks);
+  ks.tuned = ks.best >= 0;
 }
 
 void Tuner::harvest() {
@@ -327,8 +373,8 @@ void Tuner::harvest() {
       double ns = (double)ms * 1e6;
       p.ks->all_ns += ns;
       p.ks->all_images += p.images;
-      if (p.tuning) {
-        Meas &m = p.ks->meas[p.config];
+      if (p.full || p.tuning) {
+        Meas &m = p.full ? p.ks->full[p.config] : p.ks->meas[p.config];
         m.ns += ns;
         m.images += p.images;
         m.launches += 1;
@@ -336,7 +382,10 @@ void Tuner::harvest() {
     } else {
       cudaGetLastError();
     }
-    if (p.tuning) --p.ks->pending;
+    if (p.full)
+      --p.ks->fin_pending;
+    else if (p.tuning)
+      --p.ks->pending;
     pool_.push_back(p.t.start);
     pool_.push_back(p.t.stop);
     update_best(*p.ks);
@@ -380,7 +429,12 @@ void Tuner::report(fr_report *r) {
   r->tuned = ks.tuned ? 1 : 0;
   r->best_config = ks.best;
   r->last_config = ks.last_config;
-  if (ks.best >= 0) r->best_ns_per_image = ks.meas[ks.best].per_image();
+  if (ks.best >= 0) {
+    auto f = ks.full.find(ks.best);
+    r->best_ns_per_image = ks.confirmed && f != ks.full.end() && f->second.images > 0
+                               ? f->second.per_image()
+                               : ks.meas[ks.best].per_image();
+  }
   double sum = 0;
   int cnt = 0;
   for (auto &m : ks.meas)
@@ -521,6 +575,11 @@ int Tuner::load(const char *path) {
     ks.order = tuned > 0 ? std::vector<int>() : order;
     ks.next = 0;
     update_best(ks);
+    // a finished key keeps the best it was saved with (it may have been
+    // decided by whole-insert timings, which are not saved)
+    const int saved = (int)best;
+    if (tuned > 0 && saved >= 0 && saved < (int)config_space().size() && config_valid(ctx_, saved))
+      ks.best = saved;
     ks.tuned = tuned > 0 && ks.best >= 0;
     pos = e + 2;
   }

@@ -9,6 +9,16 @@
 // tuned and later inserts run the fastest configuration (the paper's
 // tuneKernelByStep behaviour once the space is exhausted).
 //
+// Sub-batch steps favour kernels whose cost has no fixed part: a gather
+// launch carries a per-launch cost (the serial path of the bricks every plane
+// crosses, the scratch merge) that a 50-image step does not amortise, so
+// ranking kernel families on sub-batches can pick a family that is slower at
+// the batch's own size.  When the screening ran in sub-batch steps, the
+// fastest configuration of each kernel family is therefore run once more on
+// a whole insert, and the key's best is the fastest of those whole-insert
+// timings (within a family the per-launch costs are alike, so the
+// sub-batch ranking stands).
+//
 // A key is (S, batch-size bucket, blob radius, image dtype): a change of image
 // size or of batch shape starts a new search (or reuses a cached one), which
 // is the runtime re-tuning of Sec. 5.3.
@@ -95,12 +105,20 @@ struct KeyState {
   bool adaptive = false;
   int budget = 0, proposed = 0;
   Walker walker;
+  // confirmation on whole inserts (see the file comment)
+  bool sub_steps = false;       // some screening step took part of an insert
+  bool confirming = false, confirmed = false;
+  std::vector<int> finalists;   // the fastest screened configuration of each family
+  size_t fin_next = 0;
+  int fin_pending = 0;
+  std::map<int, Meas> full;     // whole-insert timings of the finalists
 };
 
 struct Step {
   int config;
   int images;
   bool tuning;
+  bool full = false;  // a finalist's whole-insert timing
 };
 
 struct Timing {
@@ -114,7 +132,8 @@ class Tuner {
   KeyState &state(const TuneKey &k, fr_ctx *c);
   std::vector<Step> plan(KeyState &ks, int n, const fr_options &opt);
   Timing begin(cudaStream_t st);
-  void end(Timing t, KeyState &ks, int config, int images, bool tuning, cudaStream_t st);
+  void end(Timing t, KeyState &ks, int config, int images, bool tuning, cudaStream_t st,
+           bool full = false);
   void abandon(Timing t);
   void harvest();
   void retune(bool all);
@@ -136,6 +155,7 @@ class Tuner {
     int config;
     int images;
     bool tuning;
+    bool full;
   };
   void finish_if_done(KeyState &ks);
   void update_best(KeyState &ks);

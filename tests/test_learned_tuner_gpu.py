@@ -60,7 +60,8 @@ def test_learned_order_beats_random_on_synthetic_costs():
 
 def test_online_learned_tuning_with_shipped_model():
     S = 64
-    batches = [inputs.make_batch(S, 300, 60 + b) for b in range(4)]
+    # screening in 2-step inserts, then the kernel families' fastest on whole inserts
+    batches = [inputs.make_batch(S, 300, 60 + b) for b in range(8)]
     Vr, Wr, _ = oracle_insert(S, batches)
     ctx = L.fr_create(S)
     try:

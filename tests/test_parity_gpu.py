@@ -141,10 +141,16 @@ def test_every_configuration_matches_oracle_S128(mid_ref, cfg):
 
 
 def test_gather_is_deterministic(small_ref):
+    """With no brick split over several units (fewer than 16 images: a split
+    unit takes at least 8), every voxel is summed by one warp in a fixed
+    order, with no atomics, so two runs agree bit for bit.  Split units add
+    through float atomics, whose order (and last bits) may vary."""
     img, rot, *_ = small_ref
-    V1, W1, _ = gpu_insert(32, [(img, rot)], config=1, tuning=False)
-    V2, W2, _ = gpu_insert(32, [(img, rot)], config=1, tuning=False)
-    assert np.array_equal(V1, V2) and np.array_equal(W1, W2)
+    img, rot = img[:15], rot[:15]
+    for cfg in (1, L.fr_num_configs() - 6):  # a per-voxel and a direct-drain gather
+        V1, W1, _ = gpu_insert(32, [(img, rot)], config=cfg, tuning=False)
+        V2, W2, _ = gpu_insert(32, [(img, rot)], config=cfg, tuning=False)
+        assert np.array_equal(V1, V2) and np.array_equal(W1, W2), cfg
 
 
 @pytest.mark.parametrize("S,n,seed", [(8, 1, 5), (8, 7, 6), (16, 33, 7), (64, 37, 8), (96, 101, 9),
