@@ -12,8 +12,8 @@
 //   * each group's work units (bricks and image splits, with expected loads)
 //     are pooled over its batches with one splitting target and ordered
 //     heaviest first.  A direct-drain group is one launch with a CTA per item,
-//     plus one launch of the per-voxel gather over the items of the fold
-//     columns on a high-priority side stream beside it; a per-voxel gather
+//     plus one launch of its fold-column instantiation over the items of the
+//     fold columns on a high-priority side stream beside it; a per-voxel gather
 //     group is one persistent launch whose CTAs take items from a device
 //     counter;
 //   * the per-batch launch arguments and the items are uploaded once into a
@@ -230,7 +230,6 @@ int build_plan(Plan &pl, fr_ctx *const *ctxs, const void *const *images, const i
       // capacity): those of its first batch; the kernels read the rest per batch
       InsertArgs base = descs[kv.second.front()];
       gr.main.base = base;
-      base.fold_only = 1;
       gr.fold.base = base;
       gr.fold.priority = greatest;
       gr.lane = n_g2++ % MAX_LANES;
@@ -377,7 +376,6 @@ int prime_plan(const Plan &pl, fr_ctx *const *ctxs, const int *dtypes, const std
     } else if (k.algo == ALGO_GATHER2) {
       e = launch_gather2(k.shape, k.minw, a, nullptr, 1, nullptr);
       InsertArgs f = a;
-      f.fold_only = 1;
       f.nunits = 0;
       if (e == cudaSuccess) e = launch_gather_fold(f, nullptr);
     } else {

@@ -35,8 +35,8 @@ struct fr_ctx {
   struct Units {
     int shape = -1, n = -1, count = 0, any_split = 0, algo = 0;
     int4 *dev = nullptr;
-    // direct-drain gather: the per-voxel gather's units over the fold columns
-    // (x <= floor(a)), stored after the main units in dev
+    // direct-drain gather: the units of its fold-column launch (|x| <=
+    // floor(a)), stored after the main units in dev
     int fold_count = 0, fold_split = 0;
     const int4 *fold = nullptr;
   };

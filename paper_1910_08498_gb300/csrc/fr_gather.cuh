@@ -74,7 +74,7 @@ __device__ __forceinline__ void dot3_dd(float e0, float e1, float e2, float c0, 
   lo = (q0 + q1 + q2) + (t1 + t2);
 }
 
-// true if any column of the 8 x 4 footprint starting at (fx0, fy0) is inside the volume
+// true if any column of a warp footprint whose lowest column is (fx0, fy0) is inside the volume
 __device__ __forceinline__ bool col_in_any(const Geom &g, int fx0, int fy0) {
   return fx0 <= g.H && fy0 <= g.H;
 }
@@ -486,17 +486,18 @@ __device__ __forceinline__ int cull_step(const InsertArgs &args, float *s_list, 
 }
 
 // Fold a warp's shared partial sums (s_acc: [3][32 ZC], slot lane * ZC + t for
-// the voxel (fx0 + lane % 8, fy0 + lane / 8, z0 + t)) into HBM and clear them:
+// the voxel (fx0 + lane % FW, fy0 + lane / FW, z0 + t); FW = 8 for the 8 x 4
+// footprint, 4 for the 4 x 8 one) into HBM and clear them:
 // straight into the double-float accumulators (error-free TwoSum) when the
 // warp is the only writer of its voxels, else into the float4 scratch with
 // atomics (merged after the launch).
-template <int ZC>
+template <int ZC, int FW = 8>
 __device__ __forceinline__ void flush_partials(const InsertArgs &args, float *s_acc, int fx0,
                                                int fy0, int z0, bool to_scratch) {
   constexpr int WV = 32 * ZC;
   const Geom &g = args.g;
   const int lane = threadIdx.x & 31;
-  const int vx = fx0 + (lane & 7), vy = fy0 + (lane >> 3);
+  const int vx = fx0 + lane % FW, vy = fy0 + lane / FW;
   __syncwarp();
   if (vx <= g.H && vy <= g.H) {
 #pragma unroll
@@ -586,8 +587,6 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const Insert
   const int fx0 = g.xa0 + unit.x * BX + wx * 8;
   const int fy0 = -g.H + unit.y * BY + wy * 4;
   const int z0 = -g.H + unit.z * ZC;
-  // the direct-drain gather leaves the fold columns (x <= floor(a)) to this one
-  if (cst.fold_only && fx0 > -g.xa0) return;
   const float cx = fx0 + 3.5f, cy = fy0 + 1.5f, cz = z0 + 0.5f * (ZC - 1);  // footprint centre
   const float hz = 0.5f * (ZC - 1);
   const float rw = sqrtf(3.5f * 3.5f + 1.5f * 1.5f + hz * hz);
@@ -604,8 +603,7 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const Insert
   const int vx = fx0 + (lane & 7), vy = fy0 + (lane >> 3);
   const float dvx = (float)vx - cx, dvy = (float)vy - cy;
   const bool fold_col = vx <= -g.xa0;  // x <= floor(a): pixels from both sides of the fold
-  // with fold_only, the columns x > floor(a) belong to the direct-drain gather
-  const bool col_in = vx <= g.H && vy <= g.H && (!cst.fold_only || fold_col);
+  const bool col_in = vx <= g.H && vy <= g.H;
   const unsigned char *imgs = reinterpret_cast<const unsigned char *>(images);
   const size_t img_stride = (size_t)g.S * g.NX * ESZ;
   float2 cpair[POLY_N / 2];

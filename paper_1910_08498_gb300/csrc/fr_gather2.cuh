@@ -30,10 +30,13 @@
 // voxel has (R c)_x > 0, so a column c_x > 0 receives the stored pixel c, a
 // column c_x < 0 the stored -c conjugated, and the column c_x = 0 both (0, c_y)
 // and, conjugated, (0, -c_y): exactly what the two boxes read.  The bricks of
-// this kernel tile x >= floor(a) + 1; the fold columns x <= floor(a), where the
-// fold predicate itself has to be evaluated per pixel, are left to the
-// per-voxel gather of fr_gather.cuh, launched over those columns only
-// (fold_only).  Polynomial weights only, 4 x 4 boxes only (a < 2).
+// this kernel's main launch tile x >= floor(a) + 1.  The fold columns |x| <=
+// floor(a), where the fold predicate itself has to be evaluated per pixel,
+// are computed by a second instantiation over those columns only (FOLD), in
+// footprints 4 columns wide so that three of four lanes hold fold columns:
+// there a stored pixel k counts in the directly read box when it is not
+// folded and in the reflected box when it is (exact sign of R00 k_x + R01
+// k_y).  Polynomial weights only, 4 x 4 boxes only (a < 2).
 #pragma once
 
 #include "fr_gather.cuh"
@@ -93,11 +96,17 @@ __device__ __forceinline__ void load_row4(const unsigned char *row, float2 &p0, 
 // The 4 x 4 box of an item: candidates (kx0 + j, ky0 + l) of the stored half
 // plane (ibase points at pixel kx0 of the image), u at (kx0 + fx, ky0 + fy),
 // u_z^2 = uz2; returns the sums of w p (complex) and of w over the candidates
-// with r <= a.
-template <int F16>
+// with r <= a.  FOLD: a stored pixel k is inserted at R k when it is not
+// folded and at -R k (conjugated) when it is, folded meaning R00 k_x + R01 k_y
+// < 0 (exact sign; r00, r01 = R00, R01): the box read directly (refl = 0)
+// keeps the candidates that are not folded, the point-reflected box (refl =
+// 1) those that are.  Away from the fold columns that test always passes.
+template <int F16, int FOLD = 0>
 __device__ __forceinline__ void g2_box(const InsertArgs &args, const float2 *cp,
-                                       const unsigned char *ibase, int ky0, float fx, float fy,
-                                       float uz2, float cs, float sq, float2 &acc, float &aw) {
+                                       const unsigned char *ibase, int kx0, int ky0, float fx,
+                                       float fy, float uz2, float cs, float sq, float2 &acc,
+                                       float &aw, float r00 = 0.f, float r01 = 0.f,
+                                       bool refl = false) {
   constexpr int NP = POLY_N;
   constexpr int ESZ = F16 ? 4 : 8;
   const Geom &g = args.g;
@@ -124,8 +133,15 @@ __device__ __forceinline__ void g2_box(const InsertArgs &args, const float2 *cp,
       ha = __ffma2_rn(ha, xa, cp[k]);
       hb = __ffma2_rn(hb, xb, cp[k]);
     }
-    const float w0 = xa.x <= 1.0f ? ha.x : 0.0f, w1 = xa.y <= 1.0f ? ha.y : 0.0f;
-    const float w2_ = xb.x <= 1.0f ? hb.x : 0.0f, w3 = xb.y <= 1.0f ? hb.y : 0.0f;
+    float w0 = xa.x <= 1.0f ? ha.x : 0.0f, w1 = xa.y <= 1.0f ? ha.y : 0.0f;
+    float w2_ = xb.x <= 1.0f ? hb.x : 0.0f, w3 = xb.y <= 1.0f ? hb.y : 0.0f;
+    if (FOLD) {
+      const int kyr = ky0 + r;
+      if (fold_pred(r00, r01, kx0, kyr) != refl) w0 = 0.f;
+      if (fold_pred(r00, r01, kx0 + 1, kyr) != refl) w1 = 0.f;
+      if (fold_pred(r00, r01, kx0 + 2, kyr) != refl) w2_ = 0.f;
+      if (fold_pred(r00, r01, kx0 + 3, kyr) != refl) w3 = 0.f;
+    }
     a2 = __ffma2_rn(make_float2(w0, w0), p0, a2);
     a2 = __ffma2_rn(make_float2(w1, w1), p1, a2);
     a2 = __ffma2_rn(make_float2(w2_, w2_), p2, a2);
@@ -139,22 +155,26 @@ __device__ __forceinline__ void g2_box(const InsertArgs &args, const float2 *cp,
 // One warp's share of one work unit (see gather_warp for the unit word).
 // args: the batch's arguments; cst: the arguments its launch shares (geometry,
 // weight polynomial, list capacity) and images the batch's images, both read
-// in the inner loops.
-template <int BX, int BY, int ZC, int F16>
+// in the inner loops.  The warp footprint is FW x (32 / FW) columns (8 x 4,
+// or 4 x 8 for the fold columns).  FOLD = 0: the bricks tile x >= floor(a) +
+// 1; FOLD = 1: they tile x >= -floor(a) and only the fold columns |x| <=
+// floor(a) are computed, with the fold predicate tested per candidate.
+template <int BX, int BY, int ZC, int F16, int FW = 8, int FOLD = 0>
 __device__ __forceinline__ void gather2_warp(const InsertArgs &args, const InsertArgs &cst,
                                              const void *images, unsigned char *wsmem,
                                              const int4 unit, const int warp) {
-  static_assert(BX % 8 == 0 && BY % 4 == 0 && (BX * BY) % 32 == 0, "warp footprint is 8 x 4");
+  constexpr int FH = 32 / FW;  // footprint height in y
+  static_assert((FW == 8 || FW == 4) && BX % FW == 0 && BY % FH == 0 && (BX * BY) % 32 == 0,
+                "warp footprint is 8 x 4 or 4 x 8 columns");
   static_assert(ZC == 8 || ZC == 16, "tags hold 4 bits of z");
   constexpr int WV = 32 * ZC;
   constexpr int ESZ = F16 ? 4 : 8;
+  constexpr float HX = 0.5f * (FW - 1), HY = 0.5f * (FH - 1);  // footprint half extents
   const Geom &g = cst.g;
   const int lane = threadIdx.x & 31;
-  const int wx = warp % (BX / 8), wy = warp / (BX / 8);
-  // the bricks tile x >= floor(a) + 1: the fold columns x <= floor(a) are
-  // left to the per-voxel gather
-  const int fx0 = 1 - g.xa0 + unit.x * BX + wx * 8;
-  const int fy0 = -g.H + unit.y * BY + wy * 4;
+  const int wx = warp % (BX / FW), wy = warp / (BX / FW);
+  const int fx0 = (FOLD ? g.xa0 : 1 - g.xa0) + unit.x * BX + wx * FW;
+  const int fy0 = -g.H + unit.y * BY + wy * FH;
   const int z0 = -g.H + unit.z * ZC;
   const int lcap = cst.chunk;
   if (lcap > 64) {  // list entries are 6 bits of the tags
@@ -171,9 +191,9 @@ __device__ __forceinline__ void gather2_warp(const InsertArgs &args, const Inser
   const bool to_scratch = nsplit > 1 || ((unit.w >> 30) & 1);
   const int img0 = (int)((long long)args.n * split / nsplit);
   const int img1 = (int)((long long)args.n * (split + 1) / nsplit);
-  const float cx = fx0 + 3.5f, cy = fy0 + 1.5f, cz = z0 + 0.5f * (ZC - 1);  // footprint centre
+  const float cx = fx0 + HX, cy = fy0 + HY, cz = z0 + 0.5f * (ZC - 1);  // footprint centre
   const float hz = 0.5f * (ZC - 1);
-  const float rw = sqrtf(3.5f * 3.5f + 1.5f * 1.5f + hz * hz);
+  const float rw = sqrtf(HX * HX + HY * HY + hz * hz);
   const float a = g.a;
   // box origin ceil(u - a_box): a spare box cell (KB > floor(2a) + 1) is
   // shifted down by a margin so a pixel at distance exactly a is never lost
@@ -182,9 +202,9 @@ __device__ __forceinline__ void gather2_warp(const InsertArgs &args, const Inser
   const float a_plane = a + 1e-4f;      // conservative |u_z| <= a test
   const float reach = (float)g.H + a;   // the extended plane spans [-H, H]^2
   const float ext = reach + rw + 1.0f;
-  const int vx = fx0 + (lane & 7), vy = fy0 + (lane >> 3);
-  const bool col_in = vx <= g.H && vy <= g.H;
-  const float dvx = (float)(lane & 7) - 3.5f, dvy = (float)(lane >> 3) - 1.5f;
+  const int vx = fx0 + lane % FW, vy = fy0 + lane / FW;
+  const bool col_in = vx <= g.H && vy <= g.H && (!FOLD || vx <= -g.xa0);
+  const float dvx = (float)(lane % FW) - HX, dvy = (float)(lane / FW) - HY;
   const float cs = 2.0f / g.a2, sq = sqrtf(cs);  // the weight polynomial's argument scales
   const unsigned char *imgs = reinterpret_cast<const unsigned char *>(images);
   const size_t img_stride = (size_t)g.S * g.NX * ESZ;
@@ -217,7 +237,7 @@ __device__ __forceinline__ void gather2_warp(const InsertArgs &args, const Inser
     const float4 q1 = *reinterpret_cast<const float4 *>(L + LF_E1X);  // e1, fractional u_x
     const float4 q2 = *reinterpret_cast<const float4 *>(L + LF_E2X);  // e2, fractional u_y
     const int4 q3 = *reinterpret_cast<const int4 *>(L + LF_CIX);      // integer centre, image
-    const float sdx = (float)(src & 7) - 3.5f, sdy = (float)(src >> 3) - 1.5f,
+    const float sdx = (float)(src % FW) - HX, sdy = (float)(src / FW) - HY,
                 sdz = (float)t - hz;
     const float uz = fmaf(q0.z, sdz, fmaf(q0.y, sdy, fmaf(q0.x, sdx, q0.w)));
     const float uxr = fmaf(q1.z, sdz, fmaf(q1.y, sdy, fmaf(q1.x, sdx, q1.w)));
@@ -244,8 +264,8 @@ __device__ __forceinline__ void gather2_warp(const InsertArgs &args, const Inser
     const float fy = vyr - iyf + (float)(ky0 - kyc);
     float2 acc;
     float aw;
-    g2_box<F16>(cst, cst.poly2, imgs + (size_t)q3.z * img_stride + (size_t)kxc * ESZ, kyc, fx, fy,
-                uz * uz, cs, sq, acc, aw);
+    g2_box<F16, FOLD>(cst, cst.poly2, imgs + (size_t)q3.z * img_stride + (size_t)kxc * ESZ, kxc,
+                      kyc, fx, fy, uz * uz, cs, sq, acc, aw, q1.x, q2.x, neg);
     if (valid) {
       const int slot = src * ZC + t;
       atomicAdd(&s_acc[slot], acc.x);
@@ -341,7 +361,7 @@ __device__ __forceinline__ void gather2_warp(const InsertArgs &args, const Inser
     const bool last = cs0 >= img1;
     if (!last) {
       const long long tc = tick();
-      nl = cull_step(args, s_list, nl, cs0, img1, cx, cy, cz, 3.5f, 1.5f, hz, ext,
+      nl = cull_step(args, s_list, nl, cs0, img1, cx, cy, cz, HX, HY, hz, ext,
                      col_in_any(g, fx0, fy0));
       __syncwarp();
       if (prof && lane == 0) ph[PH_CULL] += (unsigned long long)(clock64() - tc);
@@ -354,7 +374,7 @@ __device__ __forceinline__ void gather2_warp(const InsertArgs &args, const Inser
         if (++since_flush >= GATHER_FLUSH) {
           drain(true);
           const long long tf = tick();
-          flush_partials<ZC>(args, s_acc, fx0, fy0, z0, to_scratch);
+          flush_partials<ZC, FW>(args, s_acc, fx0, fy0, z0, to_scratch);
           if (prof && lane == 0) ph[PH_FLUSH] += (unsigned long long)(clock64() - tf);
           since_flush = 0;
         }
@@ -366,7 +386,7 @@ __device__ __forceinline__ void gather2_warp(const InsertArgs &args, const Inser
     if (last) break;
   }
   const long long tf = tick();
-  flush_partials<ZC>(args, s_acc, fx0, fy0, z0, to_scratch);
+  flush_partials<ZC, FW>(args, s_acc, fx0, fy0, z0, to_scratch);
   if (prof && lane == 0) {
     ph[PH_FLUSH] += (unsigned long long)(clock64() - tf);
     ph[PH_WARP_CYCLES] = (unsigned long long)(clock64() - t_start);
@@ -377,13 +397,14 @@ __device__ __forceinline__ void gather2_warp(const InsertArgs &args, const Inser
 
 // One CTA per work unit (args.units[blockIdx.x]); warps run independently.
 // MINW: resident warps per SM the register allocation must allow (16, 20 or
-// 24: at most 128, 102 or 85 registers per thread).
-template <int BX, int BY, int ZC, int F16, int MINW>
+// 24: at most 128, 102 or 85 registers per thread).  FW, FOLD: see
+// gather2_warp.
+template <int BX, int BY, int ZC, int F16, int MINW, int FW = 8, int FOLD = 0>
 __global__ void __launch_bounds__(BX * BY, MINW * 32 / (BX * BY))
 gather2_kernel(const InsertArgs args) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5;
-  gather2_warp<BX, BY, ZC, F16>(args, args, args.images,
+  gather2_warp<BX, BY, ZC, F16, FW, FOLD>(args, args, args.images,
                                 smem + (size_t)warp * gather2_warp_smem<ZC>(args.chunk),
                                 args.units[blockIdx.x], warp);
 }
@@ -393,7 +414,7 @@ gather2_kernel(const InsertArgs args) {
 // arguments p.descs[batch] to shared memory; geometry, weight polynomial and
 // list capacity, common to the launch's batches, are read from p.base (kernel
 // parameters: constant operands in the inner loops).
-template <int BX, int BY, int ZC, int F16, int MINW>
+template <int BX, int BY, int ZC, int F16, int MINW, int FW = 8, int FOLD = 0>
 __global__ void __launch_bounds__(BX * BY, MINW * 32 / (BX * BY))
 gather2_multi_kernel(const MultiLaunch p) {
   constexpr int NT = BX * BY;
@@ -406,7 +427,7 @@ gather2_multi_kernel(const MultiLaunch p) {
   for (int i = tid; i < (int)(sizeof(InsertArgs) / 4); i += NT) dst[i] = src[i];
   __syncthreads();
   const int4 unit = make_int4(it.x & 1023, (it.x >> 10) & 1023, (it.x >> 20) & 1023, it.y);
-  gather2_warp<BX, BY, ZC, F16>(
+  gather2_warp<BX, BY, ZC, F16, FW, FOLD>(
       *s_args, p.base, p.images[it.w],
       smem + GATHER_ARGS_BYTES + (size_t)warp * gather2_warp_smem<ZC>(p.base.chunk), unit, warp);
 }

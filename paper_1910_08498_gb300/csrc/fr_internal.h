@@ -58,7 +58,6 @@ struct InsertArgs {
   const int4 *units;    // work units: (brick x, y, z, split | nsplit << 16), one per CTA
   int nunits;
   int any_split;        // 1 if some unit shares its brick with other units
-  int fold_only;        // per-voxel gather: only the fold columns (x <= floor(a)); the direct-drain gather takes the rest
   unsigned long long *phase;  // optional per-phase cycle and item counters (PH_*), or null
   // scatter
   float4 *scratch;      // [z][y][x - xa0] (re, im, w, 0)
@@ -126,8 +125,8 @@ cudaError_t launch_debug_blob(const InsertArgs &a, const float *r2, int m, int m
 // number of gather shapes and their geometry
 int num_gather_shapes();
 GatherShape gather_shape(int id);
-// the per-voxel gather over the fold columns only (fold_only set), in bricks
-// of fold_shape() (one 8-column footprint wide), polynomial weights
+// the direct-drain gather over the fold columns |x| <= floor(a) only, in
+// bricks of fold_shape() (one 4-column footprint wide), polynomial weights
 GatherShape fold_shape();
 cudaError_t launch_gather_fold(const InsertArgs &a, cudaStream_t st);
 // dynamic shared memory a gather launch needs
@@ -151,7 +150,7 @@ cudaError_t launch_gather_persistent(int shape_id, int kb, int f16, const Persis
 // share stays in the kernel parameters (base), the rest is read per batch.
 constexpr int MULTI_MAX = 64;  // batches per multi-batch launch
 struct MultiLaunch {
-  InsertArgs base;           // common arguments: geometry, weights, list capacity, fold_only
+  InsertArgs base;           // common arguments: geometry, weights, list capacity
   const InsertArgs *descs;   // device, one per batch (images, rot, n, acc, scratch, err)
   const int4 *items;         // device, {bx | by << 10 | bz << 20, split word, batch, slot}
   int nitems;
@@ -164,7 +163,7 @@ cudaError_t launch_multi(const void *fn, const MultiLaunch &p, int threads, size
 // the direct-drain gather (fold columns excluded), FP32 or FP16 images
 cudaError_t launch_gather2_multi(int shape_id, int minw, int f16, const MultiLaunch &p,
                                  cudaStream_t st);
-// the per-voxel gather over the fold columns (descs with fold_only set)
+// the direct-drain gather over the fold columns
 cudaError_t launch_gather_fold_multi(int f16, const MultiLaunch &p, cudaStream_t st);
 
 // MLP kernels

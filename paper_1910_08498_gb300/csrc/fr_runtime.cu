@@ -212,7 +212,7 @@ static int gather_units(fr_ctx *c, const Config &cfg, int n, InsertArgs &a,
   int any_split = 0, fsplit = 0;
   if (algo == ALGO_GATHER2) {
     // the direct-drain gather's bricks tile x in [floor(a) + 1, H]; the fold
-    // columns x in [-floor(a), floor(a)] go to the per-voxel gather in
+    // columns x in [-floor(a), floor(a)] go to its fold-column launch in
     // bricks one footprint wide, split finely (they are few and heavy)
     brick_unit_loads(c, gather2_shape(cfg.shape), 1 - c->g.xa0, c->g.H, n, 0.0, 32, us, any_split);
     brick_unit_loads(c, fold_shape(), c->g.xa0, -c->g.xa0, n, 0.0, 8, fs, fsplit);
@@ -300,16 +300,14 @@ int run_config(fr_ctx *c, int id, const void *images, int f16, const float *rot,
     }
     cudaError_t e;
     if (cfg.algo == ALGO_GATHER2) {
-      // the footprints with fold columns: the per-voxel gather, over those
-      // bricks only, on the side stream so that its few heavy units run
-      // beside the main launch (disjoint voxels; split units add to the
-      // scratch with atomics, merged after both)
+      // the fold columns: the fold-column instantiation, on the side stream
+      // so that its few heavy units run beside the main launch (disjoint
+      // voxels; split units add to the scratch with atomics, merged after both)
       rc = ensure_side_stream(c);
       if (rc) return rc;
       InsertArgs f = a;
       f.units = fold;
       f.nunits = nfold;
-      f.fold_only = 1;
       e = cudaEventRecord(c->ev_fork, st);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
       if (e == cudaSuccess) e = launch_gather_fold(f, c->side);
