@@ -54,12 +54,19 @@ namespace fr {
 // number of 4-byte fields per kept image in the shared-memory list: one
 // 64-byte record per image, the fields grouped by use so that each group is
 // one 16-byte load (plane normal and distance; first in-plane axis and the
-// fractional x; second axis and fractional y; integer centre and image)
+// fractional x; second axis and fractional y; integer centre and the
+// image's address)
 constexpr int LIST_FIELDS = 16;
 enum ListField {
   LF_MX, LF_MY, LF_MZ, LF_UZ, LF_E1X, LF_E1Y, LF_E1Z, LF_FX,
-  LF_E2X, LF_E2Y, LF_E2Z, LF_FY, LF_CIX, LF_CIY, LF_IMG, LF_PAD
+  LF_E2X, LF_E2Y, LF_E2Z, LF_FY, LF_CIX, LF_CIY, LF_ADLO, LF_ADHI
 };
+
+// the image address held by a list entry
+__device__ __forceinline__ const unsigned char *list_image(const float *L) {
+  const unsigned long long lo = __float_as_uint(L[LF_ADLO]), hi = __float_as_uint(L[LF_ADHI]);
+  return reinterpret_cast<const unsigned char *>(lo | (hi << 32));
+}
 
 // e . c with compensated products and sums (Ogita-Rump-Oishi Dot2), returned
 // as an unevaluated pair hi + lo; accurate to ~2^-48 relative.
@@ -443,8 +450,10 @@ __device__ __noinline__ void box_careful(const InsertArgs &args, const float2 *l
 // plane).  Kept images are appended in order to the warp's list s_list
 // (LIST_FIELDS floats per entry) starting at entry nl, with the centre's
 // projection R^T c formed with compensated products (Dot2) and split into an
-// integer part and a small remainder.  Returns the new list length.
-__device__ __forceinline__ int cull_step(const InsertArgs &args, float *s_list, int nl, int cs,
+// integer part and a small remainder, and the address of the image (imgs +
+// i img_stride, as two 32-bit halves).  Returns the new list length.
+__device__ __forceinline__ int cull_step(const InsertArgs &args, const unsigned char *imgs,
+                                         size_t img_stride, float *s_list, int nl, int cs,
                                          int img1, float cx, float cy, float cz, float hx,
                                          float hy, float hz, float ext, bool any_col) {
   const int lane = threadIdx.x & 31;
@@ -480,7 +489,9 @@ __device__ __forceinline__ int cull_step(const InsertArgs &args, float *s_list, 
     L[LF_UZ] = hzz + lz;
     L[LF_CIX] = __int_as_float((int)rx);
     L[LF_CIY] = __int_as_float((int)ry);
-    L[LF_IMG] = __int_as_float(i);
+    const unsigned long long ad = reinterpret_cast<unsigned long long>(imgs + (size_t)i * img_stride);
+    L[LF_ADLO] = __uint_as_float((unsigned)ad);
+    L[LF_ADHI] = __uint_as_float((unsigned)(ad >> 32));
   }
   return nl + __popc(bal);
 }
@@ -644,7 +655,7 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const Insert
     const float fx = uxr - ixf, fy = uyr - iyf;
     const int kx0 = LI(LF_CIX, li) + (int)ixf, ky0 = LI(LF_CIY, li) + (int)iyf;
     const float uz2 = uz * uz;
-    const unsigned char *ibase = imgs + (size_t)LI(LF_IMG, li) * img_stride;
+    const unsigned char *ibase = list_image(s_list + (size_t)li * LIST_FIELDS);
     float sr = 0.f, si = 0.f, sw = 0.f;
     if (kind == 0 || (kind == 1 && WMODE == W_POLY)) {
       if (WMODE == W_POLY) {
@@ -848,7 +859,7 @@ __device__ __forceinline__ void gather_warp(const InsertArgs &args, const Insert
     if (!last) {
       // ---- cull: one image per lane; kept images go to the warp's list in order
       const long long tc = tick();
-      nl = cull_step(args, s_list, nl, cs, img1, cx, cy, cz, 3.5f, 1.5f, hz, ext,
+      nl = cull_step(args, imgs, img_stride, s_list, nl, cs, img1, cx, cy, cz, 3.5f, 1.5f, hz, ext,
                      col_in_any(g, fx0, fy0));
       __syncwarp();
       if (prof) ph[PH_CULL] += (unsigned long long)(clock64() - tc);

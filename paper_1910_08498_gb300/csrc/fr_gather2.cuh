@@ -236,7 +236,7 @@ __device__ __forceinline__ void gather2_warp(const InsertArgs &args, const Inser
     const float4 q0 = *reinterpret_cast<const float4 *>(L + LF_MX);   // m, u_z of the centre
     const float4 q1 = *reinterpret_cast<const float4 *>(L + LF_E1X);  // e1, fractional u_x
     const float4 q2 = *reinterpret_cast<const float4 *>(L + LF_E2X);  // e2, fractional u_y
-    const int4 q3 = *reinterpret_cast<const int4 *>(L + LF_CIX);      // integer centre, image
+    const int4 q3 = *reinterpret_cast<const int4 *>(L + LF_CIX);      // integer centre, image address
     const float sdx = (float)(src % FW) - HX, sdy = (float)(src / FW) - HY,
                 sdz = (float)t - hz;
     const float uz = fmaf(q0.z, sdz, fmaf(q0.y, sdy, fmaf(q0.x, sdx, q0.w)));
@@ -264,7 +264,9 @@ __device__ __forceinline__ void gather2_warp(const InsertArgs &args, const Inser
     const float fy = vyr - iyf + (float)(ky0 - kyc);
     float2 acc;
     float aw;
-    g2_box<F16, FOLD>(cst, cst.poly2, imgs + (size_t)q3.z * img_stride + (size_t)kxc * ESZ, kxc,
+    const unsigned char *ibase = reinterpret_cast<const unsigned char *>(
+        (unsigned long long)(unsigned)q3.z | ((unsigned long long)(unsigned)q3.w << 32));
+    g2_box<F16, FOLD>(cst, cst.poly2, ibase + (size_t)kxc * ESZ, kxc,
                       kyc, fx, fy, uz * uz, cs, sq, acc, aw, q1.x, q2.x, neg);
     if (valid) {
       const int slot = src * ZC + t;
@@ -361,7 +363,7 @@ __device__ __forceinline__ void gather2_warp(const InsertArgs &args, const Inser
     const bool last = cs0 >= img1;
     if (!last) {
       const long long tc = tick();
-      nl = cull_step(args, s_list, nl, cs0, img1, cx, cy, cz, HX, HY, hz, ext,
+      nl = cull_step(args, imgs, img_stride, s_list, nl, cs0, img1, cx, cy, cz, HX, HY, hz, ext,
                      col_in_any(g, fx0, fy0));
       __syncwarp();
       if (prof && lane == 0) ph[PH_CULL] += (unsigned long long)(clock64() - tc);
