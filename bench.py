@@ -26,6 +26,9 @@ Phases (one JSON line at the end):
   stream   20 batches with a switch to S = 192 for batches 8-11 (Sec. 5.3.2
            style): tuning overhead against the oraculum, exhaustive and
            learned search, with and without the tuning cache;
+  c2       the cold-start workload (S = 128, 10 batches of 1000 images):
+           untuned, tuned, space-average rates and the online-tuning overhead
+           of the exhaustive and learned orders;
   batched  the uneven-batch workload (40 batches of S in {64..256}, n in
            [500, 5000]), FP32 and FP16 images, every batch with the
            configuration tuned for its key: one graph replay of the
@@ -71,6 +74,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the uneven-batch workload")
     p.add_argument("--no-stream", action="store_true", help="skip the 20-batch stream with an S switch")
+    p.add_argument("--no-c2", action="store_true", help="skip the S = 128 cold-start workload")
     p.add_argument("--no-fp16", action="store_true", help="skip the FP16-image measurement")
     p.add_argument("--no-recon", action="store_true", help="skip the reconstruction (last step) timing")
     p.add_argument("--no-gemm", action="store_true", help="skip the batched-GEMM dynamic-tuning study")
@@ -633,6 +637,9 @@ def run_ours(args):
     if not args.no_stream:
         stream_exp = run_stream(L, inputs, costmodel, dev, stream, batches, updates, n, f16,
                                 args.seed * 1000 + 500 + rank)
+    c2 = None
+    if not args.no_c2:
+        c2 = run_c2(L, inputs, costmodel, dev, stream, f16, args.seed * 1000 + 700 + rank)
 
     gemm_dyn = None
     if not args.no_gemm:
@@ -694,6 +701,7 @@ def run_ours(args):
         "reconstruct": recon,
         "prepare_images": prep,
         "stream": stream_exp,
+        "c2": c2,
         "batched": batched,
         "gemm_dynamic": gemm_dyn,
         "gpu_launches": args.steps * launches_per_insert(L, ctx, best, n),
@@ -941,6 +949,103 @@ def run_stream(L, inputs, costmodel, dev, stream, batches256, updates256, n, f16
         res[k] = v
         res[k.replace("_s", "_overhead_pct")] = 100.0 * (v / t_or - 1.0)
     return res
+
+
+def run_c2(L, inputs, costmodel, dev, stream, f16, seed, S=128, batches=10, n=1000):
+    """The cold-start workload of Sec. 5.3.2 (Table 10's setting): S = 128, 10
+    batches of 1000 images into one volume, online tuning over the whole
+    configuration space from a fresh context.  Reported in voxel updates/s
+    over the 10 batches: untuned (the default configuration), tuned (the
+    configuration the exhaustive search settles on, from the first batch),
+    space average (each valid configuration timed on a whole batch; the mean
+    time per image), and the stream with online tuning for the exhaustive and
+    the learned search orders: its rate, its overhead against the tuned
+    stream, and the tuner's own Eq. (performance) figure (all tuning-step
+    time against the best configuration's rate)."""
+    import torch
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    data = []
+    for _ in range(batches):
+        rot = inputs.random_rotations(n, gen, dev).contiguous()
+        img = inputs.random_images(S, n, gen, dev)
+        data.append((inputs.to_half(img) if f16 else img.contiguous(), rot))
+    probe = L.fr_create(S, 1.9, 15.0, 0, 10000)
+    ups = sum(L.fr_count_updates(probe, r) for _, r in data)
+
+    def stream_s(c):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for img, rot in data:
+            L.fr_insert(c, img, rot)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    def fresh(**opt):
+        c = L.fr_create(S, 1.9, 15.0, 0, 10000)
+        L.fr_set_options(c, **opt)
+        return c
+
+    out = {"workload": f"S={S}, {batches} batches x {n} images, one volume, a=1.9, "
+                       f"{'FP16' if f16 else 'FP32'} images, cold-start tuning",
+           "updates": ups}
+    # untuned: the default configuration
+    c = fresh(tuning=0, forced_config=-1)
+    stream_s(c)
+    L.fr_reset(c)
+    t = stream_s(c)
+    out["untuned"] = {"updates_per_s": ups / t, "config": L.fr_describe_config(
+        L.fr_tuning_report(c)["last_config"])}
+    L.fr_destroy(c)
+    # the two online searches, cold start
+    chosen = {}
+    for name, search in (("exhaustive", L.FR_SEARCH_EXHAUSTIVE), ("learned", L.FR_SEARCH_LEARNED)):
+        c = fresh(tuning=1, search=search, steps_per_insert=0, budget=0, forced_config=-1)
+        if search == L.FR_SEARCH_LEARNED:
+            costmodel.load_pretrained(c)
+        t = stream_s(c)
+        rep = L.fr_tuning_report(c)
+        extra = 0
+        while not rep["tuned"] and extra < 100:  # finish the search outside the stream
+            L.fr_insert(c, *data[extra % batches])
+            torch.cuda.synchronize()
+            rep = L.fr_tuning_report(c)
+            extra += 1
+        chosen[name] = rep["best_config"]
+        out[name] = {"updates_per_s": ups / t, "stream_s": t, "evaluated": rep["evaluated"],
+                     "space": rep["space_size"], "tuned_within_stream": extra == 0,
+                     "config": L.fr_describe_config(rep["best_config"]),
+                     "tuner_eq_performance_overhead_pct": rep["tuning_overhead_pct"]}
+        L.fr_destroy(c)
+    # tuned: the exhaustive choice from the first batch
+    c = fresh(tuning=0, forced_config=chosen["exhaustive"])
+    stream_s(c)
+    L.fr_reset(c)
+    t_tuned = stream_s(c)
+    out["tuned"] = {"updates_per_s": ups / t_tuned, "config": L.fr_describe_config(chosen["exhaustive"])}
+    for name in ("exhaustive", "learned"):
+        out[name]["overhead_vs_tuned_pct"] = 100.0 * (out[name]["stream_s"] / t_tuned - 1.0)
+    # space average: every valid configuration on one whole batch
+    img, rot = data[0]
+    per = []
+    for cfg in range(L.fr_num_configs()):
+        if not L.fr_config_valid(c, cfg):
+            continue
+        L.fr_set_options(c, tuning=0, forced_config=cfg)
+        L.fr_insert(c, img, rot)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.fr_insert(c, img, rot)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per.append(e0.elapsed_time(e1) / 1e3 / n)
+    L.fr_destroy(c)
+    L.fr_destroy(probe)
+    t_avg = sum(per) / len(per)
+    out["space_average"] = {"updates_per_s": ups / (t_avg * n * batches), "configs": len(per),
+                            "best_over_average": t_avg / min(per)}
+    return out
 
 
 def measured_hbm_gbs():

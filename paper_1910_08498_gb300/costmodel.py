@@ -19,7 +19,7 @@ k = max(1, floor(N / 10)) evaluations (the tuner's default learned budget):
   annealing, mcmc
             the library's adaptive walks over neighbouring configurations,
             simulated on the measured table (fr_search_simulate), mean over
-            20 seeds, started from the default configuration;
+            20 seeds, started from the library's default configuration;
   regret = t(kept) / t(best of all N) - 1.
 
     python -m paper_1910_08498_gb300.costmodel --train sweep_train.json \
@@ -115,17 +115,31 @@ def evaluate(ctx, wl, frac=0.10):
     return out
 
 
+DEFAULT_CONFIGS = ("gather2 bx=16 by=8 zc=8 chunk=64 warps=24 w=poly",
+                   "gather bx=16 by=16 zc=8 chunk=64 w=poly")
+
+
+def default_start(t):
+    """The library's default configuration among the measured ones of a
+    workload: the direct-drain gather 16 x 8 x 8 where it runs (a < 2), else
+    the per-voxel gather 16 x 16 x 8."""
+    desc = {L.fr_describe_config(c): c for c in t}
+    for d in DEFAULT_CONFIGS:
+        if d in desc:
+            return desc[d]
+    return min(t)
+
+
 def compare_searchers(wl, frac=0.10, seeds=20, start=None, learned=None):
     """Regret at equal budget k = max(1, floor(frac N)) of the random search
     (exact expectation), simulated annealing and the Metropolis walk (mean
     over `seeds` seeds, started from `start`, default: the library's default
     configuration) and, if given, the learned ranking ({workload: regret})."""
     ncfg = L.fr_num_configs()
-    if start is None:
-        start = 4  # gather 16 x 16 x 8, polynomial weights, 64 images per list
     rows = []
     for key, t in sorted(wl.items()):
         table = [t.get(c, 0.0) for c in range(ncfg)]
+        st = default_start(t) if start is None else start
         k = max(1, int(frac * len(t) + 1e-9))
         best = min(t.values())
         row = {"S": key[0], "a": key[1], "n": key[2], "budget": k, "configs": len(t),
@@ -133,7 +147,7 @@ def compare_searchers(wl, frac=0.10, seeds=20, start=None, learned=None):
         for name, search in (("annealing", L.FR_SEARCH_ANNEALING), ("mcmc", L.FR_SEARCH_MCMC)):
             regs = []
             for sd in range(seeds):
-                o = L.fr_search_simulate(search, table, k, seed=1000 + sd, start=start)
+                o = L.fr_search_simulate(search, table, k, seed=1000 + sd, start=st)
                 regs.append(min(table[c] for c in o) / best - 1.0)
             row[name] = float(np.mean(regs))
         if learned is not None and key in learned:

@@ -173,12 +173,14 @@ int build_plan(Plan &pl, fr_ctx *const *ctxs, const void *const *images, const i
     const GatherShape sh = g2 ? gather2_shape(gr.shape) : gather_shape(gr.shape);
     auto main_loads = [&](const fr_ctx *c, int nn, double target, std::vector<UnitLoad> &out,
                           int &split) {
-      return g2 ? brick_unit_loads(c, sh, 1 - c->g.xa0, c->g.H, nn, target, 32, out, split)
+      return g2 ? brick_unit_loads(c, sh, 1 - c->g.xa0, c->g.H, nn, target, MAIN_UNITS_PER_SM, out,
+                                   split)
                 : brick_unit_loads(c, sh, c->g.xa0, c->g.H, nn, target, 32, out, split);
     };
     auto fold_loads = [&](const fr_ctx *c, int nn, double target, std::vector<UnitLoad> &out,
                           int &split) {
-      return brick_unit_loads(c, fold_shape(), c->g.xa0, -c->g.xa0, nn, target, 8, out, split);
+      return brick_unit_loads(c, fold_shape(), c->g.xa0, -c->g.xa0, nn, target, FOLD_UNITS_PER_SM,
+                              out, split);
     };
     // pooled splitting target of the main items: total expected load over
     // 32 items per SM; the fold-column items are split as in a launch of
@@ -188,7 +190,7 @@ int build_plan(Plan &pl, fr_ctx *const *ctxs, const void *const *images, const i
     std::vector<UnitLoad> tmp;
     int any = 0;
     for (int b : kv.second) total += main_loads(ctxs[b], n[b], 1e300, tmp, any);
-    const double target = std::max(UNIT_MIN_LOAD, total / (sms * 32.0));
+    const double target = std::max(UNIT_MIN_LOAD, total / (sms * (double)MAIN_UNITS_PER_SM));
     std::vector<It> its, fits;
     for (size_t slot = 0; slot < kv.second.size(); ++slot) {
       const int b = kv.second[slot];

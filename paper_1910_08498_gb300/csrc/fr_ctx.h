@@ -80,6 +80,11 @@ double gather_unit_loads(const fr_ctx *c, int shape, int n, double target,
 // least SPLIT_MIN_IMAGES images per brick; returns the total expected load
 constexpr double UNIT_MIN_LOAD = 16.0;
 constexpr int SPLIT_MIN_IMAGES = 8;
+// units per SM of the direct-drain gather's main launch and of its fold-column
+// launch (the fold bricks are few and every plane crosses the central ones:
+// fine splits keep that launch's serial path inside the main launch's time)
+constexpr int MAIN_UNITS_PER_SM = 32;
+constexpr int FOLD_UNITS_PER_SM = 8;
 double brick_unit_loads(const fr_ctx *c, const GatherShape &sh, int x0, int x1, int n,
                         double target, int per_sm, std::vector<UnitLoad> &out, int &any_split);
 // drop cached batched-insertion plans that refer to c (called by fr_destroy)

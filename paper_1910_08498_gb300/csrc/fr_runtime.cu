@@ -214,8 +214,9 @@ static int gather_units(fr_ctx *c, const Config &cfg, int n, InsertArgs &a,
     // the direct-drain gather's bricks tile x in [floor(a) + 1, H]; the fold
     // columns x in [-floor(a), floor(a)] go to its fold-column launch in
     // bricks one footprint wide, split finely (they are few and heavy)
-    brick_unit_loads(c, gather2_shape(cfg.shape), 1 - c->g.xa0, c->g.H, n, 0.0, 32, us, any_split);
-    brick_unit_loads(c, fold_shape(), c->g.xa0, -c->g.xa0, n, 0.0, 8, fs, fsplit);
+    brick_unit_loads(c, gather2_shape(cfg.shape), 1 - c->g.xa0, c->g.H, n, 0.0, MAIN_UNITS_PER_SM,
+                     us, any_split);
+    brick_unit_loads(c, fold_shape(), c->g.xa0, -c->g.xa0, n, 0.0, FOLD_UNITS_PER_SM, fs, fsplit);
   } else {
     gather_unit_loads(c, cfg.shape, n, 0.0, us, any_split);
   }

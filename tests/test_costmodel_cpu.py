@@ -53,9 +53,14 @@ def test_shipped_model_and_sweeps_are_well_formed():
     for name in ("sweep_gb300_train.json", "sweep_gb300_heldout.json"):
         d = json.load(open(f"{cm.DATA}/{name}"))
         space = [L.fr_describe_config(i) for i in range(L.fr_num_configs())]
-        assert d["space"] == space[:len(d["space"])]
+        assert d["space"] == space  # measured on the current configuration space
         wl = cm.workloads(d["rows"])
         assert all(len(t) >= 10 and min(t.values()) > 0 for t in wl.values())
+        # every valid configuration of each workload was measured: all of the
+        # space where the direct-drain gather runs (a < 2), the rest otherwise
+        for (S, a, n), t in wl.items():
+            g2 = [i for i, s in enumerate(space) if s.startswith("gather2")]
+            assert (set(g2) <= set(t)) == (a < 2.0), (S, a, n)
 
 
 def test_search_simulate_orders():
