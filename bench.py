@@ -1123,7 +1123,7 @@ def launches_per_insert(L, ctx, cfg, n):
 
 GATHER_SOURCES = ("fr_device.cuh", "fr_gather.cuh", "fr_gather_common.cu", "fr_gather_launch.inc",
                   "fr_gather_shapes.h", "fr_internal.h", "fr_gather2.cuh", "fr_gather2.cu",
-                  "fr_gather2_launch.inc")
+                  "fr_gather2_launch.inc", "fr_gather_fold.cu", "fr_ctx.h")
 
 
 def source_hash():
